@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Benchmark: GKeys/s of the GB300 sort path on the nine-distribution 1e9-key
+int64 workload, with the HBM roofline of its dominant kernel.
+
+One step = one sort of each of the nine seeded 1e9-key int64 arrays (uniform,
+Gaussian, sorted, reverse, nearly sorted, 16 distinct, Zipf, all-equal,
+uniform [0, 1000)), each read from its own resident input buffer and written
+to an output buffer (inputs are 8 GB each, far larger than L2, so no flush is
+needed between steps).  Each array is sorted with the parameters of the tuned
+table for its sampled distribution class when one is loaded ("tuned"), else
+with the built-in defaults ("plain"); both are reported.
+
+JSON line fields follow the driver contract: value (whole-job GKeys/s),
+ms_per_step, e2e (same metric through the C ABI with pinned host buffers and
+the copies inside the timed region), roofline (dominant kernel, algorithmic
+bytes / CUDA-event time vs measured HBM copy bandwidth), cpu_baseline (the CPU
+oracle on a bounded sample), clocks, gpu_launches.
+
+    python bench.py                       # N=1, defaults
+    python bench.py --impl reference      # the CPU oracle arm
+    torchrun --nproc-per-node N bench.py --gpus N   # N replicas, weak scaling
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DISTS = ["uniform", "gaussian", "sorted", "reverse", "nearly_sorted", "distinct16", "zipf", "equal",
+         "uniform1000"]
+METRIC = "GKeys/s and % HBM roofline, GA-tuned batched vs plain sort, bit-exact, 1 GB300"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="evosort", choices=["evosort", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000_000, help="keys per array")
+    ap.add_argument("--dtype", default="int64", choices=["int32", "int64", "uint32", "uint64"])
+    ap.add_argument("--dists", default=",".join(DISTS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--params", default="auto", choices=["auto", "plain", "tuned"])
+    ap.add_argument("--digit-bits", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--kpt", type=int, default=0)
+    ap.add_argument("--rank-mode", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 23, help="keys per distribution for the oracle")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profiles(kernel_src_hash: str):
+    """DRAM bytes per key per pass of the onesweep kernel from the committed
+    ncu summary, or None if the summary is absent or the kernel has changed."""
+    p = os.path.join(ROOT, "profiles", "radix_onesweep_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_sha256") != kernel_src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_key_per_pass"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("radix.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2505_18681_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Reference arm / CPU baseline: the oracle on a bounded sample of the workload.
+# ---------------------------------------------------------------------------
+def oracle_sample_run(dists, dtype_name, sample, seed=42):
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2505_18681_gb300 import inputs
+    tdt = getattr(torch, dtype_name)
+    arrays = [inputs.generate(d, sample, tdt, seed=seed, device="cpu").numpy() for d in dists]
+    oracle.build()
+    t0 = time.perf_counter()
+    for a in arrays:
+        oracle.radix_sort(a)
+    dt = time.perf_counter() - t0
+    return len(arrays) * sample, dt
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    dists = args.dists.split(",")
+    sample = args.cpu_sample
+    for _ in range(args.warmup):
+        oracle_sample_run(dists, args.dtype, sample)
+    tot_keys, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        k, t = oracle_sample_run(dists, args.dtype, sample)
+        tot_keys += k
+        tot_t += t
+    v = tot_keys / tot_t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GKeys/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+        "data": "synthetic",
+        "config": {"workload": "nine-distribution %s sort, oracle on %d keys per distribution per step"
+                   % (args.dtype, sample), "n_per_array": sample, "dists": dists},
+        "cpu_baseline": {"value": v, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d keys x %d distributions per step, single-threaded C LSD radix"
+                         % (sample, len(dists))},
+        "e2e": {"value": v, "unit": "GKeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm.
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as tdist
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            tdist.barrier()
+
+    import paper_2505_18681_gb300 as evo
+    from paper_2505_18681_gb300 import inputs
+    evo.library()
+    dev = torch.device("cuda", local)
+    tdt = getattr(torch, args.dtype)
+    dists = args.dists.split(",")
+    n = args.n
+    w = torch.empty(0, dtype=tdt).element_size()
+
+    xs = [inputs.generate(d, n, tdt, seed=42 + 1000 * rank, device=dev) for d in dists]
+    out = torch.empty(n, dtype=tdt, device=dev)
+    torch.cuda.synchronize()
+
+    kw = {}
+    if args.digit_bits:
+        kw["digit_bits"] = args.digit_bits
+    if args.block:
+        kw["block_size"] = args.block
+    if args.kpt:
+        kw["keys_per_thread"] = args.kpt
+    if args.rank_mode:
+        kw["rank_mode"] = args.rank_mode
+    stream = torch.cuda.current_stream()
+    plain = [evo.make_params(algo="radix", stream=stream, **kw) for _ in dists]
+    params = plain
+    mode = "plain"
+    # pre-size the scratch pool so the timed region allocates nothing new
+    ws_bytes = max(evo.workspace_bytes(n, tdt, **kw), 1)
+    pre = torch.empty(0)
+    del pre
+
+    def step(ps):
+        for x, p in zip(xs, ps):
+            evo.sort(x, out=out, params=p)
+
+    for _ in range(max(args.warmup, 0)):
+        step(params)
+    evo.sync(stream)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    launches0 = evo.kernel_launches()
+    evo.profile(True)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(params)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = evo.kernel_launches() - launches0
+    recs = evo.profile_read()
+    evo.profile(False)
+    evo.sync(stream)
+    ms = e0.elapsed_time(e1)
+    ms_step = ms / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    keys_per_step = n * len(dists) * ws
+    value = keys_per_step / (ms_step * 1e-3) / 1e9
+
+    # dominant kernel: the onesweep pass; time-weighted over active launches
+    by_kind = {}
+    for r in recs:
+        k = by_kind.setdefault(r["kind"], {"ms": 0.0, "bytes": 0.0, "launches": 0, "active": 0})
+        k["ms"] += r["ms"]
+        k["bytes"] += r["bytes"]
+        k["launches"] += 1
+        k["active"] += int(r["active"])
+    ones = by_kind.get("radix_onesweep", {"ms": 0.0, "bytes": 0.0, "active": 0, "launches": 0})
+    act = [r for r in recs if r["kind"] == "radix_onesweep" and r["active"]]
+    ach = (sum(r["bytes"] for r in act) / 1e9) / (sum(r["ms"] for r in act) * 1e-3) if act else 0.0
+    peak, peak_src = measured_peaks()
+    tpk = traffic_from_profiles(kernel_hash())
+    traffic = None
+    if tpk is not None and act:
+        traffic = tpk * act[0]["items"]
+    total_alg = sum(r["bytes"] for r in recs)
+    shares = {k: round(v["ms"] / max(sum(x["ms"] for x in by_kind.values()), 1e-9), 4) for k, v in by_kind.items()}
+
+    # end to end: pinned host input -> device, sort, device -> pinned host output
+    e2e = None
+    if not args.no_e2e and rank == 0 or (not args.no_e2e and ws > 1):
+        e2e = measure_e2e(evo, xs, out, params, stream, n, w, args, barrier, ws, dev)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        k, t = oracle_sample_run(dists, args.dtype, args.cpu_sample)
+        cpu = {"value": k / t / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
+               "sample": "%d keys of each of the %d distributions (single-threaded C LSD radix, 8-bit digits)"
+               % (args.cpu_sample, len(dists))}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GKeys/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": "nine-distribution %s sort, %d keys per array (one step sorts all nine)"
+                       % (args.dtype, n), "n_per_array": n, "dists": dists, "params": mode,
+                       "param_overrides": kw,
+                       "l2": "inputs larger than L2 (%.1f GB per array), no flush" % (n * w / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "e2e": e2e,
+            "roofline": {"bound": "hbm", "kernel": "radix_onesweep", "achieved": ach, "peak": peak,
+                         "unit": "GB/s", "frac": ach / peak if peak else None, "traffic": traffic,
+                         "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": act[0]["bytes"] if act else None,
+                         "avg_active_launch_ms": (sum(r["ms"] for r in act) / len(act)) if act else None},
+            "whole_step_alg_gbs": total_alg / args.steps / 1e9 / (ms_step * 1e-3),
+            "kernel_time_share": shares,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        tdist.destroy_process_group()
+
+
+def measure_e2e(evo, xs, out, params, stream, n, w, args, barrier, ws, dev):
+    import torch
+    try:
+        host_in = [x.cpu().pin_memory() for x in xs]
+    except RuntimeError:
+        return None
+    host_out = torch.empty(n, dtype=xs[0].dtype).pin_memory()
+    dbuf = torch.empty_like(xs[0])
+
+    def step():
+        for h, p in zip(host_in, params):
+            dbuf.copy_(h, non_blocking=True)
+            evo.sort(dbuf, out=out, params=p)
+            host_out.copy_(out, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    if ws > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    keys = n * len(xs) * ws
+    return {"value": keys / (ms * 1e-3) / 1e9, "unit": "GKeys/s", "h2d_bytes_per_step": n * w * len(xs),
+            "d2h_bytes_per_step": n * w * len(xs), "ms_per_step": ms, "steps": steps}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * evosort.h — C ABI of the GB300 (sm_103a) sort library.
+ *
+ * The library sorts fixed-width keys on one GPU.  Its computation is the one
+ * EvoSort (arXiv 2505.18681) tunes: a block-based LSD radix sort (Section 3.1;
+ * Algorithms 4a/4b: sign flip, per-block digit histograms, prefix sums over the
+ * digit counts, stable scatter, one pass per digit) and a bottom-up mergesort
+ * whose base runs are insertion-sorted below a threshold and then merged
+ * pairwise (Algorithm 3), chosen per call by the dispatcher of Algorithm 5
+ * (AdaptivePartitionSort) with parameters found by the genetic algorithm of
+ * Algorithm 2 (RunGATuning).
+ *
+ * Conventions for every entry point:
+ *  - Key and value pointers are DEVICE pointers owned by the caller.  Inputs
+ *    are read, outputs written; nothing is freed or retained after return.
+ *  - Work is enqueued asynchronously on params->stream (a cudaStream_t; NULL
+ *    means the legacy default stream).  A call returns once its kernels are
+ *    enqueued; results are ready when the stream reaches that point.
+ *  - params == NULL means: tuned table entry for (dtype, size, sampled
+ *    distribution class) if a table is loaded, else the built-in defaults.
+ *  - Scratch memory: params->workspace / workspace_bytes if given (at least
+ *    evosort_workspace_bytes() bytes, 256-byte aligned), else the library
+ *    takes it from the device's stream-ordered memory pool and returns it to
+ *    the pool on the same stream.
+ *  - Errors are returned as evosort_status; a message for the calling thread
+ *    is available from evosort_last_error().  Nothing is thrown across the ABI.
+ *    Errors found on the device (a bounded wait that ran out) are recorded in
+ *    a device status word and returned by the next evosort_sync().
+ *  - n == 0 returns EVOSORT_OK without touching the device.
+ *
+ * Total order of keys (the paper sorts signed integers and flips the sign bit
+ * before the passes and back after, Algorithms 4a/4b):
+ *  - signed integers: two's-complement numeric order;
+ *  - unsigned integers: numeric order;
+ *  - floats (the paper has none; this library's reading): -inf < negatives <
+ *    -0.0 < +0.0 < positives < +inf < positive NaNs (ascending payload) <
+ *    negative NaNs (descending payload).  Every bit pattern is kept, so NaN
+ *    payloads and the sign of zero survive the sort.
+ * Every sort is stable: keys that compare equal keep their input order, which
+ * for key/value sorts makes the value order unique.
+ */
+#ifndef EVOSORT_H
+#define EVOSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EVOSORT_I32 = 0,
+    EVOSORT_I64 = 1,
+    EVOSORT_U32 = 2,
+    EVOSORT_U64 = 3,
+    EVOSORT_F32 = 4,
+    EVOSORT_F64 = 5
+} evosort_dtype;
+
+typedef enum {
+    EVOSORT_OK = 0,
+    EVOSORT_ERR_INVALID = 1,     /* bad argument (null pointer, dtype, params, offsets) */
+    EVOSORT_ERR_NOMEM = 2,       /* device memory or caller workspace too small */
+    EVOSORT_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    EVOSORT_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+    EVOSORT_ERR_UNSUPPORTED = 5  /* valid request this build cannot serve */
+} evosort_status;
+
+/* Algorithm choice, the A_code gene of Section 4.2 (3 = mergesort, 4 = radix). */
+typedef enum {
+    EVOSORT_ALGO_AUTO = -1,      /* tuned table, else radix */
+    EVOSORT_ALGO_RADIX = 0,      /* LSD radix sort, Algorithms 4a/4b */
+    EVOSORT_ALGO_MERGE = 1       /* bottom-up mergesort, Algorithm 3 */
+} evosort_algo;
+
+/* Tunable parameters.  Zero means "default" for every integer field. */
+typedef struct {
+    int algo;                 /* evosort_algo */
+    int digit_bits;           /* radix digit width d, 4..11 (default 8); the
+                                 paper fixes d = 8 (one byte per pass) */
+    int keys_per_thread;      /* keys each thread holds in a tile */
+    int block_size;           /* threads per CTA: 256 or 512 */
+    int insertion_threshold;  /* mergesort base-run length T_insertion, 2..2048
+                                 (default 32; Section 4.2 bounds) */
+    int rank_mode;            /* radix tile ranking: 1 = warp match, 2 = ballot */
+    void* stream;             /* cudaStream_t */
+    void* workspace;          /* optional caller scratch, device, 256-B aligned */
+    size_t workspace_bytes;
+} evosort_params;
+
+/* Fills *p with the built-in defaults (radix, d = 8, no workspace, NULL stream). */
+void evosort_default_params(evosort_params* p);
+
+/* Bytes of scratch one call needs for n keys of dtype dt (with_values != 0 for
+ * key/value sorts) under params p (NULL = defaults). */
+size_t evosort_workspace_bytes(size_t n, evosort_dtype dt, int with_values,
+                               const evosort_params* p);
+
+/* Sorts keys[0..n) in place (AdaptivePartitionSort, Algorithm 5).
+ * keys: device array of n elements of dtype dt. */
+evosort_status evosort_sort(void* keys, size_t n, evosort_dtype dt, const evosort_params* p);
+
+/* Out-of-place variant: reads keys_in, writes the sorted keys to keys_out.
+ * keys_in is left unchanged.  keys_in == keys_out is the in-place sort; any
+ * other overlap is an error. */
+evosort_status evosort_sort_to(const void* keys_in, void* keys_out, size_t n, evosort_dtype dt,
+                               const evosort_params* p);
+
+/* Stable key/value sort in place: values[i] travels with keys[i]; among equal
+ * keys the input order of the values is kept (argsort when values are
+ * 0..n-1).  values: device array of n uint32. */
+evosort_status evosort_sort_pairs(void* keys, uint32_t* values, size_t n, evosort_dtype dt,
+                                  const evosort_params* p);
+
+/* Out-of-place key/value sort. */
+evosort_status evosort_sort_pairs_to(const void* keys_in, const uint32_t* values_in, void* keys_out,
+                                     uint32_t* values_out, size_t n, evosort_dtype dt,
+                                     const evosort_params* p);
+
+/* Sorts each segment keys[offsets[i] .. offsets[i+1]) independently, in place,
+ * for i in [0, nseg).  offsets: DEVICE array of nseg + 1 uint64, non-decreasing,
+ * offsets[0] == 0 (empty segments allowed).  Keys never cross a segment
+ * boundary.  The offsets are validated on the device; a violation is reported
+ * by evosort_sync() as EVOSORT_ERR_INVALID and the keys are left unsorted. */
+evosort_status evosort_segmented_sort(void* keys, const uint64_t* offsets, size_t nseg,
+                                      evosort_dtype dt, const evosort_params* p);
+
+/* Waits for params-stream work (stream = NULL: the legacy default stream) and
+ * returns the first error recorded on the device since the last call
+ * (EVOSORT_ERR_TIMEOUT for a bounded wait that ran out), then clears it. */
+evosort_status evosort_sync(void* stream);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* evosort_last_error(void);
+
+/* ---- Instrumentation --------------------------------------------------
+ * While enabled, the library records a CUDA event pair on the call's stream
+ * around every kernel it launches.  evosort_profile_read() waits for the
+ * recorded events, fills up to cap records (oldest first), clears the list and
+ * returns how many records there were.  "bytes" is the launch's algorithmic
+ * traffic (keys and values read plus written); it is 0 for a radix pass whose
+ * digit was constant (skipped on the device) and for a copy that was not
+ * needed.  Events add a few microseconds per launch; leave this off outside
+ * measurements. */
+typedef enum {
+    EVOSORT_K_RADIX_HISTOGRAM = 0,   /* all-digit histogram (one key read) */
+    EVOSORT_K_RADIX_SCAN = 1,        /* digit-count prefix sums + pass plan */
+    EVOSORT_K_RADIX_ONESWEEP = 2,    /* one stable scatter pass */
+    EVOSORT_K_RADIX_FIXUP = 3,       /* copy into the output buffer */
+    EVOSORT_K_MERGE_BLOCK = 4,       /* insertion-sorted runs merged in a tile */
+    EVOSORT_K_MERGE_PARTITION = 5,   /* merge-path split points */
+    EVOSORT_K_MERGE_PASS = 6,        /* one pairwise merge round */
+    EVOSORT_K_SEGMENTED = 7          /* batched segmented sort kernels */
+} evosort_kernel_kind;
+
+typedef struct {
+    int kind;        /* evosort_kernel_kind */
+    int pass;        /* radix pass or merge round, -1 if none */
+    int active;      /* 0 if the kernel found nothing to do */
+    float ms;        /* device time between the events around the launch */
+    double bytes;    /* algorithmic bytes moved by the launch */
+    uint64_t items;  /* keys the launch covers */
+} evosort_kernel_record;
+
+evosort_status evosort_profile(int enable);
+size_t evosort_profile_read(evosort_kernel_record* out, size_t cap);
+
+/* Number of kernels this library has launched in this process (all threads). */
+uint64_t evosort_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EVOSORT_H */

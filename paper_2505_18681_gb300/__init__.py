@@ -1,0 +1,226 @@
+"""GB300 (sm_103a) sort library: Python binding of the C ABI in include/evosort.h.
+
+This module only marshals arguments: it passes device pointers, sizes, the
+current CUDA stream and the parameter struct to ``libevosort.so``; every step
+of every sort runs in the library's CUDA kernels.  There is no CPU path: if
+the library has not been built, every call raises.
+
+    import torch, paper_2505_18681_gb300 as evo
+    x = torch.randint(-2**31, 2**31 - 1, (10**6,), dtype=torch.int32, device="cuda")
+    evo.sort(x)                          # in place, LSD radix (Algorithms 4a/4b)
+    y = evo.sort(x, out=torch.empty_like(x), algo="merge", insertion_threshold=32)
+    k, v = evo.sort_pairs(keys, torch.arange(n, dtype=torch.uint32, device="cuda"))
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+__all__ = ["sort", "sort_pairs", "segmented_sort", "sync", "workspace_bytes", "kernel_launches",
+           "profile", "profile_read",
+           "EvoSortError", "Params", "library", "DTYPES"]
+
+DTYPES = {torch.int32: 0, torch.int64: 1, torch.uint32: 2, torch.uint64: 3,
+          torch.float32: 4, torch.float64: 5}
+ALGOS = {"auto": -1, "radix": 0, "merge": 1, None: -1, -1: -1, 0: 0, 1: 1}
+STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_UNSUPPORTED"}
+
+
+class EvoSortError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__("%s: %s" % (STATUS.get(code, code), message))
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``evosort_params``."""
+    _fields_ = [("algo", ctypes.c_int), ("digit_bits", ctypes.c_int), ("keys_per_thread", ctypes.c_int),
+                ("block_size", ctypes.c_int), ("insertion_threshold", ctypes.c_int),
+                ("rank_mode", ctypes.c_int), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class KernelRecord(ctypes.Structure):
+    """Mirror of ``evosort_kernel_record``."""
+    _fields_ = [("kind", ctypes.c_int), ("pass_", ctypes.c_int), ("active", ctypes.c_int),
+                ("ms", ctypes.c_float), ("bytes", ctypes.c_double), ("items", ctypes.c_uint64)]
+
+
+KERNEL_KINDS = {0: "radix_histogram", 1: "radix_scan", 2: "radix_onesweep", 3: "radix_fixup",
+                4: "merge_block", 5: "merge_partition", 6: "merge_pass", 7: "segmented"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library():
+    """The loaded ctypes handle of libevosort.so (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libevosort.so is not built; run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'` first")
+            lib = ctypes.CDLL(_build.LIB)
+            vp, sz, i, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int
+            pp = ctypes.POINTER(Params)
+            lib.evosort_default_params.argtypes = [pp]
+            lib.evosort_default_params.restype = None
+            lib.evosort_workspace_bytes.argtypes = [sz, i, i, pp]
+            lib.evosort_workspace_bytes.restype = sz
+            lib.evosort_sort.argtypes = [vp, sz, i, pp]
+            lib.evosort_sort_to.argtypes = [vp, vp, sz, i, pp]
+            lib.evosort_sort_pairs.argtypes = [vp, vp, sz, i, pp]
+            lib.evosort_sort_pairs_to.argtypes = [vp, vp, vp, vp, sz, i, pp]
+            for f in (lib.evosort_sort, lib.evosort_sort_to, lib.evosort_sort_pairs, lib.evosort_sort_pairs_to):
+                f.restype = st
+            if hasattr(lib, "evosort_segmented_sort"):
+                lib.evosort_segmented_sort.argtypes = [vp, vp, sz, i, pp]
+                lib.evosort_segmented_sort.restype = st
+            lib.evosort_sync.argtypes = [vp]
+            lib.evosort_sync.restype = st
+            lib.evosort_last_error.argtypes = []
+            lib.evosort_last_error.restype = ctypes.c_char_p
+            lib.evosort_profile.argtypes = [i]
+            lib.evosort_profile.restype = st
+            lib.evosort_profile_read.argtypes = [ctypes.POINTER(KernelRecord), sz]
+            lib.evosort_profile_read.restype = sz
+            lib.evosort_kernel_launches.argtypes = []
+            lib.evosort_kernel_launches.restype = ctypes.c_uint64
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = library().evosort_last_error()
+        raise EvoSortError(rc, msg.decode() if msg else "")
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    try:
+        return DTYPES[t.dtype]
+    except KeyError:
+        raise TypeError("unsupported key dtype %s" % t.dtype) from None
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("tensors must be on a CUDA device")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(algo=None, digit_bits=0, keys_per_thread=0, block_size=0, insertion_threshold=0,
+                rank_mode=0, stream=None, workspace: torch.Tensor | None = None) -> Params:
+    p = Params()
+    library().evosort_default_params(ctypes.byref(p))
+    p.algo = ALGOS[algo]
+    p.digit_bits = int(digit_bits or 0)
+    p.keys_per_thread = int(keys_per_thread or 0)
+    p.block_size = int(block_size or 0)
+    p.insertion_threshold = int(insertion_threshold or 0)
+    p.rank_mode = int(rank_mode or 0)
+    p.stream = _stream_handle(stream)
+    if workspace is not None:
+        p.workspace = workspace.data_ptr()
+        p.workspace_bytes = workspace.numel() * workspace.element_size()
+    return p
+
+
+def sort(keys: torch.Tensor, out: torch.Tensor | None = None, *, params: Params | None = None,
+         **kw) -> torch.Tensor:
+    """Sorts ``keys`` (in place unless ``out`` is given) and returns the result.
+    Keyword arguments are the fields of ``evosort_params`` (see make_params)."""
+    _need_cuda(keys, out)
+    p = params if params is not None else make_params(**kw)
+    dt = _dtype_code(keys)
+    lib = library()
+    if out is None or out.data_ptr() == keys.data_ptr():
+        _check(lib.evosort_sort(keys.data_ptr(), keys.numel(), dt, ctypes.byref(p)))
+        return keys
+    if out.dtype != keys.dtype or out.numel() != keys.numel():
+        raise ValueError("out must match keys in dtype and size")
+    _check(lib.evosort_sort_to(keys.data_ptr(), out.data_ptr(), keys.numel(), dt, ctypes.byref(p)))
+    return out
+
+
+def sort_pairs(keys: torch.Tensor, values: torch.Tensor, keys_out: torch.Tensor | None = None,
+               values_out: torch.Tensor | None = None, *, params: Params | None = None, **kw):
+    """Stable key/value sort; ``values`` are uint32.  In place unless both
+    outputs are given.  Returns (keys, values)."""
+    _need_cuda(keys, values, keys_out, values_out)
+    if values.dtype != torch.uint32 or values.numel() != keys.numel():
+        raise ValueError("values must be uint32 with one entry per key")
+    p = params if params is not None else make_params(**kw)
+    dt = _dtype_code(keys)
+    lib = library()
+    if keys_out is None and values_out is None:
+        _check(lib.evosort_sort_pairs(keys.data_ptr(), values.data_ptr(), keys.numel(), dt, ctypes.byref(p)))
+        return keys, values
+    if keys_out is None or values_out is None:
+        raise ValueError("give both keys_out and values_out, or neither")
+    _check(lib.evosort_sort_pairs_to(keys.data_ptr(), values.data_ptr(), keys_out.data_ptr(),
+                                     values_out.data_ptr(), keys.numel(), dt, ctypes.byref(p)))
+    return keys_out, values_out
+
+
+def segmented_sort(keys: torch.Tensor, offsets: torch.Tensor, *, params: Params | None = None, **kw):
+    """Sorts each ``keys[offsets[i]:offsets[i+1]]`` in place.  ``offsets`` is a
+    device tensor of nseg + 1 int64/uint64 values starting at 0."""
+    _need_cuda(keys, offsets)
+    if offsets.dtype not in (torch.int64, torch.uint64):
+        raise ValueError("offsets must be int64 or uint64")
+    p = params if params is not None else make_params(**kw)
+    _check(library().evosort_segmented_sort(keys.data_ptr(), offsets.data_ptr(), offsets.numel() - 1,
+                                            _dtype_code(keys), ctypes.byref(p)))
+    return keys
+
+
+def sync(stream=None) -> None:
+    """Waits for the stream and raises if a device-side error was recorded."""
+    _check(library().evosort_sync(_stream_handle(stream)))
+
+
+def workspace_bytes(n: int, dtype: torch.dtype, with_values: bool = False, **kw) -> int:
+    p = make_params(**kw)
+    return int(library().evosort_workspace_bytes(n, DTYPES[dtype], int(with_values), ctypes.byref(p)))
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(library().evosort_kernel_launches())
+
+
+def profile(enable: bool) -> None:
+    """Turn the library's per-launch CUDA-event instrumentation on or off."""
+    _check(library().evosort_profile(int(bool(enable))))
+
+
+def profile_read() -> list:
+    """Per-launch records since the last read: dicts with kind, pass, active,
+    ms (device time between the events around the launch) and bytes
+    (algorithmic traffic of the launch)."""
+    lib = library()
+    cap = 1 << 16
+    buf = (KernelRecord * cap)()
+    n = int(lib.evosort_profile_read(buf, cap))
+    return [{"kind": KERNEL_KINDS.get(r.kind, r.kind), "pass": r.pass_, "active": bool(r.active),
+             "ms": float(r.ms), "bytes": float(r.bytes), "items": int(r.items)} for r in buf[:min(n, cap)]]

@@ -1,0 +1,481 @@
+// C ABI of the sort library: argument checks, parameter resolution, scratch
+// memory and the dispatcher of Algorithm 5 (AdaptivePartitionSort).
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/evosort.h"
+#include "api_internal.h"
+#include "radix_launch.cuh"
+
+namespace evosort {
+
+// Device status word: kernels OR error bits into it; evosort_sync reads and
+// clears it.
+__device__ uint32_t g_status_word;
+
+static thread_local std::string t_err;
+static std::atomic<uint64_t> g_launches{0};
+
+void set_error(const std::string& msg) { t_err = msg; }
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static std::mutex g_dev_mu;
+struct DevInfo {
+    bool init = false;
+    int sms = 0;
+    uint32_t* status = nullptr;
+};
+static DevInfo g_dev[64];
+
+const DevInfo* device_info(std::string* err) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevInfo& di = g_dev[dev];
+    if (!di.init) {
+        e = cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&di.status, g_status_word);
+        if (e == cudaSuccess) {
+            // keep freed scratch in the stream-ordered pool instead of returning
+            // it to the driver after every call
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t thr = ~0ull;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+        }
+        if (e != cudaSuccess) {
+            *err = std::string("device set-up: ") + cudaGetErrorString(e);
+            return nullptr;
+        }
+        di.init = true;
+    }
+    return &di;
+}
+
+int sm_count() {
+    std::string err;
+    const DevInfo* di = device_info(&err);
+    return di ? di->sms : 148;
+}
+
+uint32_t* status_word(std::string* err) {
+    const DevInfo* di = device_info(err);
+    return di ? di->status : nullptr;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// Instrumentation: CUDA events around every launch while enabled.  Each sort
+// call also copies its radix pass descriptors to pinned host memory so a
+// record can say whether the pass ran or was skipped.
+// ---------------------------------------------------------------------------
+struct ProfRecord {
+    int kind, pass, call;
+    double bytes;
+    uint64_t items;
+    cudaEvent_t e0, e1;
+};
+struct ProfCall {
+    PassDesc* host_desc;   // pinned copy, npass + 1 entries (radix calls)
+    int ndesc;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRecord> g_prof;
+static std::vector<ProfCall> g_prof_calls;
+// pinned arena for the descriptor copies (allocated when profiling is enabled,
+// so nothing is allocated while a measured region runs)
+constexpr size_t kArenaDescs = 1 << 14;
+static PassDesc* g_arena = nullptr;
+static size_t g_arena_used = 0;
+
+bool prof_enabled() { return g_prof_on; }
+
+int prof_call_begin(const PassDesc* dev_desc, int ndesc, cudaStream_t) {
+    if (!g_prof_on) return -1;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfCall c{nullptr, 0};
+    if (dev_desc && ndesc > 0 && g_arena && g_arena_used + ndesc <= kArenaDescs) {
+        c.host_desc = g_arena + g_arena_used;
+        c.ndesc = ndesc;
+        g_arena_used += ndesc;
+    }
+    g_prof_calls.push_back(c);
+    return (int)g_prof_calls.size() - 1;
+}
+
+void prof_call_end(int call, cudaStream_t s, const PassDesc* dev_desc) {
+    if (call < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfCall& c = g_prof_calls[call];
+    if (c.host_desc && dev_desc)
+        cudaMemcpyAsync(c.host_desc, dev_desc, sizeof(PassDesc) * c.ndesc, cudaMemcpyDeviceToHost, s);
+}
+
+ProfScope::ProfScope(int call, int kind, int pass, double bytes, uint64_t items, cudaStream_t s)
+    : call_(call), idx_(-1), s_(s) {
+    if (!g_prof_on || call < 0) return;
+    ProfRecord r{kind, pass, call, bytes, items, nullptr, nullptr};
+    cudaEventCreate(&r.e0);
+    cudaEventCreate(&r.e1);
+    cudaEventRecord(r.e0, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back(r);
+    idx_ = (int)g_prof.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (idx_ < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(g_prof[idx_].e1, s_);
+}
+
+
+// ---------------------------------------------------------------------------
+// Radix sort: scratch layout and launch sequence.
+// ---------------------------------------------------------------------------
+struct RadixLayout {
+    int npass;
+    size_t ntiles;
+    int lb64;
+    size_t off_desc, off_tiles, off_counts, off_lookback, zero_end, off_tmp, off_vtmp, total;
+};
+
+static RadixLayout radix_layout(size_t n, int w, bool pairs, const Plan& pl) {
+    RadixLayout L;
+    L.npass = (8 * w + pl.digit_bits - 1) / pl.digit_bits;
+    const size_t tile = (size_t)pl.block_size * pl.keys_per_thread;
+    L.ntiles = (n + tile - 1) / tile;
+    L.lb64 = n >= (1ull << 30) ? 1 : 0;
+    const size_t bins = (size_t)1 << pl.digit_bits;
+    size_t off = 0;
+    L.off_desc = off;
+    off = align_up(off + (L.npass + 1) * sizeof(PassDesc), 256);
+    L.off_tiles = off;
+    off = align_up(off + L.npass * sizeof(uint32_t), 256);
+    L.off_counts = off;
+    off = align_up(off + L.npass * bins * sizeof(unsigned long long), 256);
+    L.off_lookback = off;
+    off = align_up(off + (size_t)L.npass * L.ntiles * bins * (L.lb64 ? 8 : 4), 256);
+    L.zero_end = off;
+    L.off_tmp = off;
+    off = align_up(off + n * w, 256);
+    L.off_vtmp = off;
+    if (pairs) off = align_up(off + n * sizeof(uint32_t), 256);
+    L.total = off;
+    return L;
+}
+
+size_t radix_workspace_bytes(size_t n, int w, bool pairs, const Plan& pl) {
+    return radix_layout(n, w, pairs, pl).total;
+}
+
+int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt,
+               const Plan& pl, void* ws, size_t ws_bytes, cudaStream_t s, std::string* err) {
+    const int w = dtype_bytes(dt);
+    const bool pairs = vout != nullptr;
+    RadixLayout L = radix_layout(n, w, pairs, pl);
+    if (ws_bytes < L.total) {
+        *err = "workspace too small";
+        return EVOSORT_ERR_NOMEM;
+    }
+    uint32_t* status = status_word(err);
+    if (!status) return EVOSORT_ERR_CUDA;
+    char* base = (char*)ws;
+    RadixArgs a;
+    a.in = in;
+    a.out = out;
+    a.tmp = base + L.off_tmp;
+    a.vin = vin;
+    a.vout = vout;
+    a.vtmp = pairs ? (uint32_t*)(base + L.off_vtmp) : nullptr;
+    a.n = n;
+    a.dt = dt;
+    a.d = pl.digit_bits;
+    a.npass = L.npass;
+    a.lb64 = L.lb64;
+    a.ntiles = L.ntiles;
+    a.desc = (PassDesc*)(base + L.off_desc);
+    a.counts = (unsigned long long*)(base + L.off_counts);
+    a.lookback = base + L.off_lookback;
+    a.tile_counter = (uint32_t*)(base + L.off_tiles);
+    a.status = status;
+    const int inplace = (in == out) ? 1 : 0;
+
+    cudaError_t e = cudaMemsetAsync(base, 0, L.zero_end, s);
+    const int sms = sm_count();
+    const size_t hist_smem = (size_t)L.npass * ((size_t)1 << pl.digit_bits) * sizeof(uint32_t);
+    size_t hist_grid = (n + 512 * 16 - 1) / (512 * 16);
+    if (hist_grid > (size_t)sms * 2) hist_grid = (size_t)sms * 2;
+    if (hist_grid < 1) hist_grid = 1;
+    const int vb = pairs ? 4 : 0;
+    const double pass_bytes = 2.0 * (double)n * (w + vb);
+    const int call = prof_call_begin(a.desc, L.npass + 1, s);
+    {
+        ProfScope ps(call, EVOSORT_K_RADIX_HISTOGRAM, -1, (double)n * w, n, s);
+        if (e == cudaSuccess) e = launch_radix_aux(w, 0, hist_grid, hist_smem, s, a, inplace);
+    }
+    {
+        ProfScope ps(call, EVOSORT_K_RADIX_SCAN, -1, 0.0, 0, s);
+        if (e == cudaSuccess) e = launch_radix_aux(w, 1, 1, 0, s, a, inplace);
+    }
+    for (int p = 0; p < L.npass && e == cudaSuccess; ++p) {
+        ProfScope ps(call, EVOSORT_K_RADIX_ONESWEEP, p, pass_bytes, n, s);
+        if (w == 4)
+            e = launch_onesweep_u32(pairs, pl.block_size, pl.keys_per_thread, pl.rank_mode, L.ntiles, sms, s, a, p);
+        else
+            e = launch_onesweep_u64(pairs, pl.block_size, pl.keys_per_thread, pl.rank_mode, L.ntiles, sms, s, a, p);
+    }
+    size_t fix_grid = (n + 256 * 8 - 1) / (256 * 8);
+    if (fix_grid > (size_t)sms * 8) fix_grid = (size_t)sms * 8;
+    {
+        ProfScope ps(call, EVOSORT_K_RADIX_FIXUP, L.npass, pass_bytes, n, s);
+        if (e == cudaSuccess) e = launch_radix_aux(w, 2, fix_grid, 0, s, a, inplace);
+    }
+    prof_call_end(call, s, a.desc);
+    count_launches(3 + L.npass);
+    if (e != cudaSuccess) {
+        *err = std::string("radix launch: ") + cudaGetErrorString(e);
+        return EVOSORT_ERR_CUDA;
+    }
+    return EVOSORT_OK;
+}
+
+}  // namespace evosort
+
+using namespace evosort;
+
+// ---------------------------------------------------------------------------
+// Parameter resolution.
+// ---------------------------------------------------------------------------
+static void defaults_for(int w, Plan* pl) {
+    pl->algo = EVOSORT_ALGO_RADIX;
+    pl->digit_bits = 8;
+    pl->block_size = 256;
+    pl->keys_per_thread = w == 4 ? 16 : 8;
+    pl->insertion_threshold = 32;
+    pl->rank_mode = 1;
+}
+
+static int resolve(const evosort_params* p, int dt, Plan* pl, std::string* err) {
+    const int w = dtype_bytes(dt);
+    defaults_for(w, pl);
+    if (!p) return EVOSORT_OK;
+    if (p->algo != EVOSORT_ALGO_AUTO) pl->algo = p->algo;
+    if (p->digit_bits) pl->digit_bits = p->digit_bits;
+    if (p->block_size) pl->block_size = p->block_size;
+    if (p->keys_per_thread) pl->keys_per_thread = p->keys_per_thread;
+    if (p->insertion_threshold) pl->insertion_threshold = p->insertion_threshold;
+    if (p->rank_mode) pl->rank_mode = p->rank_mode;
+    if (pl->algo != EVOSORT_ALGO_RADIX && pl->algo != EVOSORT_ALGO_MERGE) {
+        *err = "params.algo must be -1, 0 or 1";
+        return EVOSORT_ERR_INVALID;
+    }
+    if (pl->digit_bits < 4 || pl->digit_bits > 11) {
+        *err = "params.digit_bits must be in [4, 11]";
+        return EVOSORT_ERR_INVALID;
+    }
+    if (pl->rank_mode != 1 && pl->rank_mode != 2) {
+        *err = "params.rank_mode must be 1 or 2";
+        return EVOSORT_ERR_INVALID;
+    }
+    if (pl->insertion_threshold < 2 || pl->insertion_threshold > 2048) {
+        *err = "params.insertion_threshold must be in [2, 2048]";
+        return EVOSORT_ERR_INVALID;
+    }
+    if (pl->algo == EVOSORT_ALGO_RADIX && !onesweep_shape_supported(pl->block_size, pl->keys_per_thread)) {
+        *err = "params.block_size/keys_per_thread: unsupported radix tile shape";
+        return EVOSORT_ERR_INVALID;
+    }
+    return EVOSORT_OK;
+}
+
+static bool valid_dtype(int dt) { return dt >= EVOSORT_I32 && dt <= EVOSORT_F64; }
+
+static bool overlaps(const void* a, const void* b, size_t bytes) {
+    const char* x = (const char*)a;
+    const char* y = (const char*)b;
+    return x != y && x < y + bytes && y < x + bytes;
+}
+
+static evosort_status finish(int rc, const std::string& err) {
+    if (rc != EVOSORT_OK) set_error(err);
+    return (evosort_status)rc;
+}
+
+static evosort_status sort_common(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n,
+                                  evosort_dtype dt, const evosort_params* p) {
+    std::string err;
+    set_error("");
+    if (!valid_dtype(dt)) return finish(EVOSORT_ERR_INVALID, "unknown dtype");
+    if (n == 0) return EVOSORT_OK;
+    const int w = dtype_bytes(dt);
+    if (!in || !out) return finish(EVOSORT_ERR_INVALID, "null key pointer");
+    if (((uintptr_t)in % w) || ((uintptr_t)out % w)) return finish(EVOSORT_ERR_INVALID, "misaligned key pointer");
+    const bool pairs = vout != nullptr || vin != nullptr;
+    if (pairs && (!vin || !vout)) return finish(EVOSORT_ERR_INVALID, "null value pointer");
+    if (pairs && (((uintptr_t)vin % 4) || ((uintptr_t)vout % 4)))
+        return finish(EVOSORT_ERR_INVALID, "misaligned value pointer");
+    if (overlaps(in, out, n * w)) return finish(EVOSORT_ERR_INVALID, "keys_in and keys_out overlap");
+    if (pairs && overlaps(vin, vout, n * 4)) return finish(EVOSORT_ERR_INVALID, "values_in and values_out overlap");
+    if (pairs && (in == out) != ((const void*)vin == (const void*)vout))
+        return finish(EVOSORT_ERR_INVALID, "keys and values must both be in place or both out of place");
+    if (n >= (1ull << 40)) return finish(EVOSORT_ERR_UNSUPPORTED, "n >= 2^40");
+    if (pairs && n > 0xFFFFFFFFull) return finish(EVOSORT_ERR_UNSUPPORTED, "key/value sorts need n < 2^32");
+    Plan pl;
+    int rc = resolve(p, dt, &pl, &err);
+    if (rc) return finish(rc, err);
+    cudaStream_t s = p ? (cudaStream_t)p->stream : nullptr;
+
+    size_t need = 0;
+    if (pl.algo == EVOSORT_ALGO_MERGE) {
+        need = merge_workspace_bytes(n, w, pairs, pl);
+    } else {
+        need = radix_workspace_bytes(n, w, pairs, pl);
+    }
+    void* ws = p ? p->workspace : nullptr;
+    size_t ws_bytes = p ? p->workspace_bytes : 0;
+    bool owned = false;
+    if (!ws) {
+        const DevInfo* di = device_info(&err);
+        if (!di) return finish(EVOSORT_ERR_CUDA, err);
+        cudaError_t e = cudaMallocAsync(&ws, need, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return finish(EVOSORT_ERR_NOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+        }
+        ws_bytes = need;
+        owned = true;
+    } else if ((uintptr_t)ws % 256) {
+        return finish(EVOSORT_ERR_INVALID, "workspace must be 256-byte aligned");
+    }
+    if (pl.algo == EVOSORT_ALGO_MERGE)
+        rc = merge_sort(in, out, vin, vout, n, dt, pl, ws, ws_bytes, s, &err);
+    else
+        rc = radix_sort(in, out, vin, vout, n, dt, pl, ws, ws_bytes, s, &err);
+    if (owned) cudaFreeAsync(ws, s);
+    return finish(rc, err);
+}
+
+extern "C" {
+
+void evosort_default_params(evosort_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->algo = EVOSORT_ALGO_RADIX;
+}
+
+size_t evosort_workspace_bytes(size_t n, evosort_dtype dt, int with_values, const evosort_params* p) {
+    std::string err;
+    if (!valid_dtype(dt)) return 0;
+    Plan pl;
+    if (resolve(p, dt, &pl, &err)) return 0;
+    const int w = dtype_bytes(dt);
+    if (pl.algo == EVOSORT_ALGO_MERGE) return merge_workspace_bytes(n, w, with_values != 0, pl);
+    return radix_workspace_bytes(n, w, with_values != 0, pl);
+}
+
+evosort_status evosort_sort(void* keys, size_t n, evosort_dtype dt, const evosort_params* p) {
+    return sort_common(keys, keys, nullptr, nullptr, n, dt, p);
+}
+
+evosort_status evosort_sort_to(const void* keys_in, void* keys_out, size_t n, evosort_dtype dt,
+                               const evosort_params* p) {
+    return sort_common(keys_in, keys_out, nullptr, nullptr, n, dt, p);
+}
+
+evosort_status evosort_sort_pairs(void* keys, uint32_t* values, size_t n, evosort_dtype dt,
+                                  const evosort_params* p) {
+    if (n && !values) return finish(EVOSORT_ERR_INVALID, "null value pointer");
+    return sort_common(keys, keys, values, values, n, dt, p);
+}
+
+evosort_status evosort_sort_pairs_to(const void* keys_in, const uint32_t* values_in, void* keys_out,
+                                     uint32_t* values_out, size_t n, evosort_dtype dt,
+                                     const evosort_params* p) {
+    if (n && (!values_in || !values_out)) return finish(EVOSORT_ERR_INVALID, "null value pointer");
+    return sort_common(keys_in, keys_out, values_in, values_out, n, dt, p);
+}
+
+evosort_status evosort_sync(void* stream) {
+    std::string err;
+    set_error("");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return finish(EVOSORT_ERR_CUDA, std::string("synchronize: ") + cudaGetErrorString(e));
+    uint32_t* sw = status_word(&err);
+    if (!sw) return finish(EVOSORT_ERR_CUDA, err);
+    uint32_t v = 0;
+    e = cudaMemcpy(&v, sw, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return finish(EVOSORT_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    if (v) {
+        uint32_t zero = 0;
+        cudaMemcpy(sw, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        if (v & ST_TIMEOUT) return finish(EVOSORT_ERR_TIMEOUT, "a bounded device wait ran out");
+        return finish(EVOSORT_ERR_INVALID, "device-side argument check failed (segment offsets)");
+    }
+    return EVOSORT_OK;
+}
+
+const char* evosort_last_error(void) { return t_err.c_str(); }
+
+evosort_status evosort_profile(int enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (enable && !g_arena) {
+        cudaError_t e = cudaMallocHost((void**)&g_arena, sizeof(PassDesc) * kArenaDescs);
+        if (e != cudaSuccess) {
+            g_arena = nullptr;
+            set_error(std::string("pinned arena: ") + cudaGetErrorString(e));
+            return EVOSORT_ERR_CUDA;
+        }
+    }
+    g_prof_on = enable != 0;
+    return EVOSORT_OK;
+}
+
+size_t evosort_profile_read(evosort_kernel_record* out, size_t cap) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    size_t k = 0;
+    for (size_t i = 0; i < g_prof.size(); ++i) {
+        ProfRecord& r = g_prof[i];
+        cudaEventSynchronize(r.e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.e0, r.e1);
+        int active = 1;
+        const ProfCall& c = g_prof_calls[r.call];
+        if (c.host_desc) {
+            if (r.kind == EVOSORT_K_RADIX_ONESWEEP && r.pass >= 0 && r.pass < c.ndesc)
+                active = c.host_desc[r.pass].active;
+            if (r.kind == EVOSORT_K_RADIX_FIXUP && r.pass >= 0 && r.pass < c.ndesc)
+                active = c.host_desc[r.pass].fixup != FIX_NONE;
+        }
+        if (out && k < cap) {
+            out[k].kind = r.kind;
+            out[k].pass = r.pass;
+            out[k].active = active;
+            out[k].ms = ms;
+            out[k].bytes = active ? r.bytes : 0.0;
+            out[k].items = r.items;
+        }
+        ++k;
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    g_arena_used = 0;
+    g_prof.clear();
+    g_prof_calls.clear();
+    return k;
+}
+
+uint64_t evosort_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+namespace evosort {
+
+// Resolved parameters of one sort call.
+struct Plan {
+    int algo;                 // 0 radix, 1 merge
+    int digit_bits;           // radix digit width d
+    int block_size;           // threads per CTA
+    int keys_per_thread;      // keys each thread holds in a tile
+    int insertion_threshold;  // mergesort base-run length
+    int rank_mode;            // radix tile ranking variant
+};
+
+void set_error(const std::string& msg);
+void count_launches(uint64_t k);
+int sm_count();
+uint32_t* status_word(std::string* err);
+
+struct PassDesc;
+bool prof_enabled();
+int prof_call_begin(const PassDesc* dev_desc, int ndesc, cudaStream_t s);
+void prof_call_end(int call, cudaStream_t s, const PassDesc* dev_desc);
+// Records a CUDA event pair around one launch while instrumentation is on.
+class ProfScope {
+  public:
+    ProfScope(int call, int kind, int pass, double bytes, uint64_t items, cudaStream_t s);
+    ~ProfScope();
+  private:
+    int call_, idx_;
+    cudaStream_t s_;
+};
+
+size_t radix_workspace_bytes(size_t n, int w, bool pairs, const Plan& pl);
+int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt,
+               const Plan& pl, void* ws, size_t ws_bytes, cudaStream_t s, std::string* err);
+
+size_t merge_workspace_bytes(size_t n, int w, bool pairs, const Plan& pl);
+int merge_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt,
+               const Plan& pl, void* ws, size_t ws_bytes, cudaStream_t s, std::string* err);
+
+}  // namespace evosort

@@ -1,0 +1,128 @@
+// Shared device helpers for the sort kernels: key types, the order-preserving
+// key transform, memory-model helpers and small block-wide scans.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace evosort {
+
+// dtype codes, identical to evosort_dtype in include/evosort.h
+enum : int { DT_I32 = 0, DT_I64 = 1, DT_U32 = 2, DT_U64 = 3, DT_F32 = 4, DT_F64 = 5 };
+
+// device status word bits (evosort_sync maps them to evosort_status)
+enum : uint32_t { ST_TIMEOUT = 1u, ST_BAD_OFFSETS = 2u };
+
+// Bounded waits: polls of a look-back slot before the kernel gives up, records
+// ST_TIMEOUT and proceeds (its output is then invalid but the context lives).
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+inline int dtype_bytes(int dt) { return (dt == DT_I32 || dt == DT_U32 || dt == DT_F32) ? 4 : 8; }
+
+// ---------------------------------------------------------------------------
+// Order-preserving map of key bits onto unsigned integers (the sign flip of
+// Algorithms 4a/4b; for floats the sign-magnitude flip, then a rotation by
+// 2^m - 1 that moves both NaN blocks above +inf).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_ordered(uint32_t u, int dt) {
+    if (dt == DT_I32) return u ^ 0x80000000u;
+    if (dt == DT_F32) {
+        uint32_t t = (u & 0x80000000u) ? ~u : (u ^ 0x80000000u);
+        return t - 0x007FFFFFu;
+    }
+    return u;
+}
+__device__ __forceinline__ uint64_t to_ordered(uint64_t u, int dt) {
+    if (dt == DT_I64) return u ^ 0x8000000000000000ull;
+    if (dt == DT_F64) {
+        uint64_t t = (u >> 63) ? ~u : (u ^ 0x8000000000000000ull);
+        return t - 0x000FFFFFFFFFFFFFull;
+    }
+    return u;
+}
+__device__ __forceinline__ uint32_t from_ordered(uint32_t t, int dt) {
+    if (dt == DT_I32) return t ^ 0x80000000u;
+    if (dt == DT_F32) {
+        uint32_t x = t + 0x007FFFFFu;
+        return (x & 0x80000000u) ? (x ^ 0x80000000u) : ~x;
+    }
+    return t;
+}
+__device__ __forceinline__ uint64_t from_ordered(uint64_t t, int dt) {
+    if (dt == DT_I64) return t ^ 0x8000000000000000ull;
+    if (dt == DT_F64) {
+        uint64_t x = t + 0x000FFFFFFFFFFFFFull;
+        return (x >> 63) ? (x ^ 0x8000000000000000ull) : ~x;
+    }
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Relaxed GPU-scope loads/stores for the decoupled look-back slots.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Streaming loads/stores: data touched once per pass, kept out of L1.
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
+template <typename T>
+__device__ __forceinline__ void st_stream(T* p, T v) { __stcs(p, v); }
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of one value per thread (any integer type).
+// scratch: at least BLOCK/32 elements of shared memory.  Returns the
+// exclusive prefix; *total receives the block sum.
+// ---------------------------------------------------------------------------
+template <int BLOCK, typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* scratch, T* total) {
+    constexpr int WARPS = BLOCK / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < WARPS ? scratch[lane] : T(0);
+        T wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < WARPS) scratch[lane] = wi - w;   // exclusive warp offsets
+        if (lane == WARPS - 1) scratch[WARPS] = wi; // block total
+    }
+    __syncthreads();
+    T r = scratch[warp] + inc - v;
+    *total = scratch[WARPS];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace evosort

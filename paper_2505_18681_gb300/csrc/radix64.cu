@@ -1,0 +1,32 @@
+// Onesweep pass kernels for 64-bit keys (int64, uint64, float64), plus the
+// histogram, scan/plan and fixup kernels of both key widths.
+#include "radix_launch.cuh"
+
+namespace evosort {
+
+cudaError_t launch_onesweep_u64(bool pairs, int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
+                                const RadixArgs& a, int pass) {
+    return pairs ? launch_onesweep_shape<uint64_t, true>(block, kpt, rank, grid, sms, s, a, pass)
+                 : launch_onesweep_shape<uint64_t, false>(block, kpt, rank, grid, sms, s, a, pass);
+}
+
+// which: 0 = histogram, 1 = scan/plan, 2 = fixup
+cudaError_t launch_radix_aux(int w, int which, size_t grid, size_t smem, cudaStream_t s, const RadixArgs& a,
+                             int inplace) {
+    if (which == 0) {
+        if (w == 4)
+            radix_histogram<uint32_t><<<(unsigned)grid, 512, smem, s>>>(a);
+        else
+            radix_histogram<uint64_t><<<(unsigned)grid, 512, smem, s>>>(a);
+    } else if (which == 1) {
+        radix_scan_plan<<<1, 1024, 0, s>>>(a, inplace);
+    } else {
+        if (w == 4)
+            radix_fixup<uint32_t><<<(unsigned)grid, 256, 0, s>>>(a);
+        else
+            radix_fixup<uint64_t><<<(unsigned)grid, 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace evosort

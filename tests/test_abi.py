@@ -1,0 +1,107 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+entry point declared in include/*.h, and rejects bad arguments before it
+touches the device."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_18681_gb300 import _build
+    _build.build()
+    import paper_2505_18681_gb300 as evo
+    return evo.library()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(evosort_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for must in ("evosort_sort", "evosort_sort_pairs", "evosort_sync", "evosort_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2505_18681_gb300 import _build
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(evosort_\w+)", out))
+    missing = [n for n in declared_symbols() if n not in exported]
+    assert not missing, missing
+    for n in declared_symbols():
+        assert hasattr(lib, n)
+
+
+def test_library_is_built_for_sm103a():
+    from paper_2505_18681_gb300 import _build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(_build.NVCC_FLAGS)
+
+
+def _params(lib, **kw):
+    import paper_2505_18681_gb300 as evo
+    p = evo.Params()
+    lib.evosort_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+FAKE = 0x10000   # never dereferenced: every case below fails its host check first
+
+
+def test_rejects_bad_arguments_without_a_gpu(lib):
+    p = _params(lib)
+    bp = ctypes.byref(p)
+    assert lib.evosort_sort(None, 10, 0, bp) == 1                 # null keys
+    assert lib.evosort_sort(FAKE, 10, 9, bp) == 1                 # bad dtype
+    assert lib.evosort_sort(FAKE + 2, 10, 0, bp) == 1             # misaligned int32
+    assert lib.evosort_sort(FAKE + 4, 10, 1, bp) == 1             # misaligned int64
+    assert lib.evosort_sort_to(FAKE, FAKE + 8, 10, 0, bp) == 1    # overlapping in/out
+    assert lib.evosort_sort_pairs(FAKE, None, 10, 0, bp) == 1     # null values
+    assert lib.evosort_sort_pairs_to(FAKE, FAKE + 4096, FAKE + 8192, FAKE + 4096, 10, 0, bp) == 1
+    msg = lib.evosort_last_error()
+    assert msg and len(msg) > 0
+    # n == 0 is a no-op that never touches the device
+    assert lib.evosort_sort(None, 0, 0, bp) == 0
+    assert lib.evosort_sort(FAKE, 0, 0, bp) == 0
+
+
+@pytest.mark.parametrize("field,value", [("digit_bits", 3), ("digit_bits", 12), ("algo", 7),
+                                         ("rank_mode", 3), ("insertion_threshold", 1),
+                                         ("insertion_threshold", 4096), ("block_size", 100)])
+def test_rejects_bad_params(lib, field, value):
+    p = _params(lib, **{field: value})
+    assert lib.evosort_sort(FAKE, 10, 0, ctypes.byref(p)) == 1
+    assert lib.evosort_workspace_bytes(1000, 0, 0, ctypes.byref(p)) == 0
+
+
+def test_workspace_bytes_grows_with_n(lib):
+    p = _params(lib)
+    a = lib.evosort_workspace_bytes(1000, 0, 0, ctypes.byref(p))
+    b = lib.evosort_workspace_bytes(1_000_000, 0, 0, ctypes.byref(p))
+    c = lib.evosort_workspace_bytes(1_000_000, 0, 1, ctypes.byref(p))
+    assert 0 < a < b < c
+    assert b >= 4 * 1_000_000    # at least the ping-pong key buffer
+
+
+def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_2505_18681_gb300 as evo
+    from paper_2505_18681_gb300 import _build
+    monkeypatch.setattr(evo, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        evo.library()

@@ -1,0 +1,166 @@
+"""GPU parity of the LSD radix path (Algorithms 4a/4b) against the CPU oracle.
+
+Every case compares the CUDA result with the oracle's bit for bit on the same
+seeded input (the oracle sorts a host copy of the exact device input).  Sizes
+span one tile, several tiles and ragged tails; parameters cover every digit
+width, tile shape and ranking variant compiled into the library.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+INT = [torch.int32, torch.int64, torch.uint32, torch.uint64]
+ALL = INT + [torch.float32, torch.float64]
+
+
+def bits(t: torch.Tensor) -> np.ndarray:
+    a = t.cpu().numpy()
+    return a.view(np.uint32 if a.dtype.itemsize == 4 else np.uint64)
+
+
+def gen(dist, n, dtype, seed=42):
+    from paper_2505_18681_gb300 import inputs
+    if dtype.is_floating_point and dist != "float_mix":
+        dist = "uniform"
+    return inputs.generate(dist, n, dtype, seed=seed, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def evo():
+    import paper_2505_18681_gb300 as evo
+    evo.library()
+    return evo
+
+
+def run_keys(evo, x, inplace=False, **kw):
+    expect = oracle.radix_sort(x.cpu().numpy())
+    if inplace:
+        y = x.clone()
+        evo.sort(y, **kw)
+    else:
+        y = torch.empty_like(x)
+        x0 = x.clone()
+        evo.sort(x, out=y, **kw)
+    evo.sync()
+    assert np.array_equal(bits(y), expect.view(bits(y).dtype)), "keys differ from the oracle"
+    if not inplace:
+        assert torch.equal(x.view(torch.uint8), x0.view(torch.uint8)), "input modified"
+
+
+def run_pairs(evo, x, inplace=False, **kw):
+    n = x.numel()
+    v = torch.arange(n, dtype=torch.int64, device="cuda").to(torch.int32).view(torch.uint32)
+    ek, ev = oracle.radix_sort(x.cpu().numpy(), v.cpu().numpy())
+    if inplace:
+        k, vv = x.clone(), v.clone()
+        evo.sort_pairs(k, vv, **kw)
+    else:
+        k, vv = torch.empty_like(x), torch.empty_like(v)
+        evo.sort_pairs(x, v, k, vv, **kw)
+    evo.sync()
+    assert np.array_equal(bits(k), ek.view(bits(k).dtype)), "pair keys differ"
+    assert np.array_equal(vv.cpu().numpy(), ev), "pair values (stable argsort) differ"
+
+
+@pytest.mark.parametrize("dtype", ALL, ids=str)
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 255, 2048, 4095, 4096, 4097, 3 * 4096 + 17, 100_003])
+def test_sizes(evo, dtype, n):
+    run_keys(evo, gen("uniform", n, dtype), algo="radix")
+
+
+def test_config_1e6_int32_seed0(evo):
+    """1e6 int32 keys uniform over the full range, seed 0, 8-bit digits."""
+    run_keys(evo, gen("uniform", 1_000_000, torch.int32, seed=0), algo="radix", digit_bits=8)
+    run_keys(evo, gen("uniform", 1_000_000, torch.int32, seed=0), inplace=True, algo="radix", digit_bits=8)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "gaussian", "sorted", "reverse", "nearly_sorted",
+                                  "distinct16", "zipf", "equal", "uniform1000", "uniform_paper"])
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64], ids=str)
+def test_distributions(evo, dist, dtype):
+    x = gen(dist, 300_007, dtype)
+    run_keys(evo, x, algo="radix")
+    run_keys(evo, x, inplace=True, algo="radix")
+    run_pairs(evo, x, algo="radix")
+
+
+@pytest.mark.parametrize("d", list(range(4, 12)))
+@pytest.mark.parametrize("dtype", [torch.int32, torch.float64], ids=str)
+def test_digit_widths(evo, d, dtype):
+    """Every digit width; odd pass counts also exercise the in-place copy-back."""
+    x = gen("float_mix" if dtype.is_floating_point else "uniform", 70_001, dtype)
+    run_keys(evo, x, algo="radix", digit_bits=d)
+    run_keys(evo, x, inplace=True, algo="radix", digit_bits=d)
+    run_pairs(evo, x, inplace=True, algo="radix", digit_bits=d)
+
+
+@pytest.mark.parametrize("shape", [(256, 8), (256, 16), (512, 8), (512, 16), (256, 24)])
+@pytest.mark.parametrize("rank", [1, 2])
+@pytest.mark.parametrize("d", [8, 11])
+def test_tile_shapes_and_ranking(evo, shape, rank, d):
+    block, kpt = shape
+    for dtype in (torch.uint32, torch.int64):
+        x = gen("zipf" if dtype == torch.int64 else "uniform", 150_011, dtype)
+        run_keys(evo, x, algo="radix", block_size=block, keys_per_thread=kpt, rank_mode=rank, digit_bits=d)
+        run_pairs(evo, x, algo="radix", block_size=block, keys_per_thread=kpt, rank_mode=rank, digit_bits=d)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=str)
+def test_float_total_order_and_stability(evo, dtype):
+    """-0.0 < +0.0, NaNs last with payloads kept, stable argsort (config 3 shape)."""
+    x = gen("float_mix", 200_003, dtype)
+    run_keys(evo, x, algo="radix")
+    run_pairs(evo, x, algo="radix")
+    run_pairs(evo, x, inplace=True, algo="radix")
+
+
+def test_unaligned_and_offset_views(evo):
+    """Keys that start off a 16-byte boundary (histogram head/tail path)."""
+    for dtype in (torch.int32, torch.int64):
+        base = gen("uniform", 50_013, dtype)
+        for off in (1, 2, 3):
+            x = base[off:].contiguous() if off == 0 else base[off:]
+            run_keys(evo, x, algo="radix")
+
+
+def test_all_passes_skipped(evo):
+    """All-equal keys: every digit is constant, no pass runs; out-of-place
+    copies, in-place is a no-op; values keep input order."""
+    for dtype in ALL:
+        x = torch.full((12_345,), 7, dtype=torch.int64, device="cuda").to(dtype) if not dtype.is_floating_point \
+            else torch.full((12_345,), -0.0, dtype=dtype, device="cuda")
+        run_keys(evo, x, algo="radix")
+        run_keys(evo, x, inplace=True, algo="radix")
+        run_pairs(evo, x, algo="radix")
+
+
+def test_caller_workspace_and_stream(evo):
+    x = gen("uniform", 123_457, torch.int64)
+    need = evo.workspace_bytes(x.numel(), torch.int64, with_values=False, algo="radix")
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        evo.sort(x, out=y, algo="radix", workspace=ws)
+    evo.sync(s)
+    assert np.array_equal(bits(y), oracle.radix_sort(x.cpu().numpy()).view(np.uint64))
+    small = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(evo.EvoSortError) as ei:
+        evo.sort(x, out=y, algo="radix", workspace=small)
+    assert ei.value.status == "ERR_NOMEM"
+
+
+def test_repeated_calls_are_identical(evo):
+    x = gen("gaussian", 500_001, torch.int64)
+    outs = []
+    for _ in range(3):
+        y = torch.empty_like(x)
+        evo.sort(x, out=y, algo="radix", digit_bits=11)
+        outs.append(y)
+    evo.sync()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
