@@ -264,7 +264,7 @@ static void defaults_for(int w, Plan* pl) {
     pl->block_size = 256;
     pl->keys_per_thread = w == 4 ? 16 : 8;
     pl->insertion_threshold = 32;
-    pl->rank_mode = 1;
+    pl->rank_mode = 2;
 }
 
 static int resolve(const evosort_params* p, int dt, Plan* pl, std::string* err) {
@@ -335,6 +335,10 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     Plan pl;
     int rc = resolve(p, dt, &pl, &err);
     if (rc) return finish(rc, err);
+    if (pl.algo == EVOSORT_ALGO_RADIX &&
+        !onesweep_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits))
+        return finish(EVOSORT_ERR_INVALID, "radix tile does not fit in shared memory (block_size x "
+                                           "keys_per_thread too large for this key width and digit width)");
     cudaStream_t s = p ? (cudaStream_t)p->stream : nullptr;
 
     size_t need = 0;

@@ -203,6 +203,12 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
 // ---------------------------------------------------------------------------
 // K3: one onesweep pass.  RANK selects how a warp finds the lanes that share
 // a digit: 1 = match.any, 2 = one ballot per digit bit.
+//
+// Persistent CTAs take tiles in order from an atomic counter, so every tile's
+// predecessors are held by running CTAs and the look-back always progresses.
+// A CTA claims its next tile while it works on the current one and has the
+// TMA engine copy that tile (keys, and values for pairs) into the other half
+// of a double input buffer; a third buffer receives the reordered tile.
 // ---------------------------------------------------------------------------
 template <int RANK>
 __device__ __forceinline__ uint32_t warp_peers(uint32_t dig, int d) {
@@ -218,232 +224,286 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t dig, int d) {
     }
 }
 
-template <int BLOCK, int KPT, int MAXB, bool PAIRS, typename U>
-constexpr size_t onesweep_smem_bytes(int d) {
-    return (size_t)BLOCK * KPT * sizeof(U) + (PAIRS ? (size_t)BLOCK * KPT * 4 : 0) +
-           (size_t)(BLOCK / 32) * (1u << d) * 2 + (size_t)(1u << d) * 4 + (size_t)(1u << d) * 8;
+// Dynamic shared memory of one onesweep CTA: three tile buffers (two TMA
+// input buffers, one reorder buffer), per-warp digit counters, the tile's
+// digit offsets and global bases, two mbarriers.
+__host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d) {
+    return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * ((size_t)1 << d) * 2 +
+           ((size_t)1 << d) * 4 + ((size_t)1 << d) * 8 + 16;
+}
+// Largest dynamic shared memory a CTA may use on sm_100-class GPUs (227 KB),
+// less room for the kernel's static shared variables.
+constexpr size_t kMaxDynSmem = 232448 - 1024;
+
+// Decoupled look-back for one digit: sums the counts of the preceding tiles
+// back to the nearest inclusive prefix.  LBW slots are read per L2 round trip.
+template <typename S, int LBW>
+__device__ __forceinline__ uint64_t lookback_digit(const S* slot0, size_t stride, long long tile,
+                                                   uint32_t* status) {
+    constexpr int FB = sizeof(S) * 8 - 2;   // flag bits: 01 aggregate, 10 inclusive prefix
+    const S cmask = ((S)1 << FB) - 1;
+    uint64_t excl = 0;
+    long long t = tile - 1;
+    uint32_t polls = 0;
+    while (t >= 0) {
+        S v[LBW];
+#pragma unroll
+        for (int k = 0; k < LBW; ++k)
+            v[k] = (t - k >= 0) ? ld_relaxed(slot0 + (size_t)(t - k) * stride) : ((S)2 << FB);
+        int adv = 0;
+        bool fin = false, blocked = false;
+#pragma unroll
+        for (int k = 0; k < LBW; ++k) {
+            if (!fin && !blocked) {
+                const uint32_t f = (uint32_t)(v[k] >> FB);
+                if (f == 0) {
+                    blocked = true;
+                } else {
+                    excl += (uint64_t)(v[k] & cmask);
+                    ++adv;
+                    if (f == 2) fin = true;
+                }
+            }
+        }
+        if (fin) break;
+        t -= adv;
+        if (blocked) {
+            if (++polls > kSpinLimit) {
+                atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+            if ((polls & 255u) == 0 && ld_relaxed(status) != 0) break;
+            __nanosleep(32);
+        }
+    }
+    return excl;
 }
 
 template <typename U, bool PAIRS, int BLOCK, int KPT, int MAXB, int RANK>
-__global__ void __launch_bounds__(BLOCK) radix_onesweep(RadixArgs a, int pass) {
+__global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(RadixArgs a, int pass) {
     constexpr int WARPS = BLOCK / 32;
     constexpr int TILE = BLOCK * KPT;
     constexpr int PER_MAX = ((1 << MAXB) + BLOCK - 1) / BLOCK;
+    constexpr size_t KB = (size_t)TILE * sizeof(U);
+    constexpr size_t VB = PAIRS ? (size_t)TILE * 4 : 0;
     const PassDesc desc = a.desc[pass];
     if (!desc.active) return;
 
     const int d = a.d;
     const int bins = 1 << d;
     const int shift = pass * d;
-    const U mask = (U)(bins - 1);
+    const uint32_t mask = (uint32_t)(bins - 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    U* s_keys = (U*)smem;
-    uint32_t* s_vals = (uint32_t*)(smem + (size_t)TILE * sizeof(U));
-    uint16_t* s_whist = (uint16_t*)(smem + (size_t)TILE * sizeof(U) + (PAIRS ? (size_t)TILE * 4 : 0));
+    unsigned char* bufs = smem;   // two input tile buffers of KB + VB bytes
+    U* s_rkeys = (U*)(smem + 2 * (KB + VB));                  // reorder buffer
+    uint32_t* s_rvals = (uint32_t*)(smem + 2 * (KB + VB) + KB);
+    uint16_t* s_whist = (uint16_t*)(smem + 3 * (KB + VB));
     uint32_t* s_excl = (uint32_t*)(s_whist + WARPS * bins);
     unsigned long long* s_gbase = (unsigned long long*)(s_excl + bins);
-    __shared__ uint32_t s_tile;
+    uint64_t* s_bar = (uint64_t*)(s_gbase + bins);
+    __shared__ uint32_t s_tile[2];
     __shared__ uint32_t s_scr[WARPS + 1];
 
     const size_t n = a.n;
     const U* src = sel_src<U>(a, desc.src);
     U* dst = sel_dst<U>(a, desc.dst);
+    const uint32_t* vsrc = PAIRS ? sel_vsrc(a, desc.src) : nullptr;
+    uint32_t* vdst = PAIRS ? sel_vdst(a, desc.dst) : nullptr;
+    const bool use_tma = (((uintptr_t)src & 15) == 0) && (!PAIRS || (((uintptr_t)vsrc & 15) == 0));
+    const size_t full_tiles = n / TILE;
 
-    // Persistent CTAs: tiles are taken in order from an atomic counter, so a
-    // tile's predecessors are always held by running CTAs (forward progress
-    // of the look-back does not depend on CTA scheduling order).
-    for (;;) {
-    if (tid == 0) s_tile = atomicAdd(a.tile_counter + pass, 1u);
-    {
-        uint32_t* z = (uint32_t*)s_whist;
-        for (int i = tid; i < WARPS * bins / 2; i += BLOCK) z[i] = 0;
-    }
-    __syncthreads();
-    const size_t tile = s_tile;
-    if (tile >= a.ntiles) break;
-    const size_t base = tile * TILE;
-
-    // ---- load (warp-striped: each warp reads a contiguous run of 32*KPT keys)
-    U key[KPT];
-    uint32_t val[PAIRS ? KPT : 1];
-    const size_t wbase = base + (size_t)warp * 32 * KPT + lane;
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-        const size_t idx = wbase + (size_t)i * 32;
-        if (idx < n) {
-            U k = ld_stream(src + idx);
-            key[i] = desc.xin ? to_ordered(k, a.dt) : k;
-        } else {
-            key[i] = ~(U)0;   // pad: ranks after every real key of the tile
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_mbar_init();
+        const uint32_t t0 = atomicAdd(a.tile_counter + pass, 1u);
+        s_tile[0] = t0;
+        if (use_tma && t0 < full_tiles) {
+            mbar_arrive_expect_tx(&s_bar[0], (uint32_t)(KB + VB));
+            bulk_load(bufs, src + (size_t)t0 * TILE, (uint32_t)KB, &s_bar[0]);
+            if (PAIRS) bulk_load(bufs + KB, vsrc + (size_t)t0 * TILE, (uint32_t)VB, &s_bar[0]);
         }
     }
-    if (PAIRS) {
-        const uint32_t* vsrc = sel_vsrc(a, desc.src);
+    __syncthreads();
+
+    uint32_t ph0 = 0, ph1 = 0;   // mbarrier phase of each buffer
+    const uint32_t FA32 = 1u << 30, FP32 = 2u << 30;
+    const uint64_t FA64 = 1ull << 62, FP64 = 2ull << 62;
+
+    for (int it = 0;; ++it) {
+        const int cur = it & 1;
+        const uint32_t tile = s_tile[cur];
+        if (tile >= a.ntiles) break;
+        const size_t base = (size_t)tile * TILE;
+        const bool full = tile < full_tiles;
+        // claim the next tile and start copying it into the other buffer
+        if (tid == 0) {
+            const uint32_t nx = atomicAdd(a.tile_counter + pass, 1u);
+            s_tile[cur ^ 1] = nx;
+            if (use_tma && nx < full_tiles) {
+                unsigned char* nb = bufs + (cur ^ 1) * (KB + VB);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&s_bar[cur ^ 1], (uint32_t)(KB + VB));
+                bulk_load(nb, src + (size_t)nx * TILE, (uint32_t)KB, &s_bar[cur ^ 1]);
+                if (PAIRS) bulk_load(nb + KB, vsrc + (size_t)nx * TILE, (uint32_t)VB, &s_bar[cur ^ 1]);
+            }
+        }
+        unsigned char* kb = bufs + cur * (KB + VB);
+        U* s_keys = (U*)kb;
+        uint32_t* s_vals = (uint32_t*)(kb + KB);
+        uint16_t* wh = s_whist + warp * bins;
+        for (int i = lane; i < bins / 2; i += 32) ((uint32_t*)wh)[i] = 0;
+
+        // ---- keys of the tile, warp-striped (warp w owns a contiguous run of
+        // 32*KPT keys; key i of a lane sits at w*32*KPT + 32*i + lane).  The
+        // keys stay in the tile buffer until the reorder; registers keep only
+        // (rank << 16 | digit) per key.
+        uint32_t dr[KPT];
+        const int wofs = warp * 32 * KPT + lane;
+        if (use_tma && full) {
+            const uint32_t ph = cur ? ph1 : ph0;
+            mbar_wait_bounded(&s_bar[cur], ph, a.status);
+            if (cur) ph1 ^= 1u; else ph0 ^= 1u;
+#pragma unroll
+            for (int i = 0; i < KPT; ++i) {
+                U k = s_keys[wofs + 32 * i];
+                if (desc.xin) k = to_ordered(k, a.dt);
+                dr[i] = digit_of(k, shift, mask);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < KPT; ++i) {
+                const size_t idx = base + wofs + 32 * i;
+                U k = ~(U)0;   // pad: ranks after every real key of the tile
+                if (idx < n) {
+                    const U raw = ld_stream(src + idx);
+                    s_keys[wofs + 32 * i] = raw;
+                    if (PAIRS) s_vals[wofs + 32 * i] = ld_stream(vsrc + idx);
+                    k = desc.xin ? to_ordered(raw, a.dt) : raw;
+                }
+                dr[i] = digit_of(k, shift, mask);
+            }
+        }
+        __syncwarp();
+
+        // ---- stable rank of each key among the equal digits of its warp
+        const uint32_t lt = lanemask_lt();
 #pragma unroll
         for (int i = 0; i < KPT; ++i) {
-            const size_t idx = wbase + (size_t)i * 32;
-            val[i] = idx < n ? ld_stream(vsrc + idx) : 0u;
+            const uint32_t dig = dr[i];
+            const uint32_t peers = warp_peers<RANK>(dig, d);
+            const int leader = 31 - __clz(peers);
+            uint32_t old = 0;
+            if (lane == leader) {
+                old = wh[dig];
+                wh[dig] = (uint16_t)(old + __popc(peers));
+            }
+            old = __shfl_sync(0xffffffffu, old, leader);
+            dr[i] = dig | ((old + __popc(peers & lt)) << 16);
+            __syncwarp();
         }
-    }
+        __syncthreads();
 
-    // ---- stable rank of each key among equal digits of its warp
-    uint16_t* wh = s_whist + warp * bins;
-    uint32_t rank[KPT];
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-        const uint32_t dig = (uint32_t)((key[i] >> shift) & mask);
-        const uint32_t peers = warp_peers<RANK>(dig, d);
-        const int leader = 31 - __clz(peers);
-        uint32_t old = 0;
-        if (lane == leader) {
-            old = wh[dig];
-            wh[dig] = (uint16_t)(old + __popc(peers));
-        }
-        old = __shfl_sync(0xffffffffu, old, leader);
-        rank[i] = old + __popc(peers & lt);
-        __syncwarp();
-    }
-    __syncthreads();
-
-    // ---- tile digit counts; warp counts -> exclusive prefix over warps
-    const int per = (bins + BLOCK - 1) / BLOCK;
-    const int b0 = tid * per;
-    uint32_t cnt[PER_MAX];
-    uint32_t mysum = 0;
-#pragma unroll
-    for (int j = 0; j < PER_MAX; ++j) {
-        cnt[j] = 0;
-        const int b = b0 + j;
-        if (j < per && b < bins) {
-            uint32_t s = 0;
-#pragma unroll 4
-            for (int w = 0; w < WARPS; ++w) {
-                const uint32_t c = s_whist[w * bins + b];
-                s_whist[w * bins + b] = (uint16_t)s;
-                s += c;
-            }
-            cnt[j] = s;
-            mysum += s;
-        }
-    }
-    // publish this tile's aggregate (tile 0 publishes its inclusive prefix)
-    const uint32_t FA32 = 1u << 30, FP32 = 2u << 30, M32 = FA32 - 1;
-    const uint64_t FA64 = 1ull << 62, FP64 = 2ull << 62, M64 = FA64 - 1;
-#pragma unroll
-    for (int j = 0; j < PER_MAX; ++j) {
-        const int b = b0 + j;
-        if (j < per && b < bins) {
-            const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
-            if (a.lb64)
-                st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | cnt[j]);
-            else
-                st_relaxed((uint32_t*)a.lookback + slot, (tile == 0 ? FP32 : FA32) | cnt[j]);
-        }
-    }
-    // exclusive scan of the tile counts over digits
-    {
-        uint32_t tot;
-        uint32_t ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tot);
+        // ---- tile digit counts; warp counts -> exclusive prefix over warps
+        const int per = (bins + BLOCK - 1) / BLOCK;
+        const int b0 = tid * per;
+        uint32_t cnt[PER_MAX];
+        uint32_t mysum = 0;
 #pragma unroll
         for (int j = 0; j < PER_MAX; ++j) {
-            const int b = b0 + j;
-            if (j < per && b < bins) s_excl[b] = ex;
-            ex += cnt[j];
-        }
-    }
-    // ---- decoupled look-back over preceding tiles, all owned digits at once
-    {
-        uint64_t excl[PER_MAX];
-        long long t[PER_MAX];
-        bool done[PER_MAX];
-        int left = 0;
-#pragma unroll
-        for (int j = 0; j < PER_MAX; ++j) {
-            excl[j] = 0;
-            t[j] = (long long)tile - 1;
-            done[j] = !(j < per && b0 + j < bins) || tile == 0;
-            left += done[j] ? 0 : 1;
-        }
-        uint32_t polls = 0;
-        while (left > 0) {
-#pragma unroll
-            for (int j = 0; j < PER_MAX; ++j) {
-                if (done[j]) continue;
-                const size_t slot = ((size_t)pass * a.ntiles + (size_t)t[j]) * bins + b0 + j;
-                uint64_t v, flag, c;
-                if (a.lb64) {
-                    v = ld_relaxed((const uint64_t*)a.lookback + slot);
-                    flag = v >> 62;
-                    c = v & M64;
-                } else {
-                    const uint32_t v32 = ld_relaxed((const uint32_t*)a.lookback + slot);
-                    flag = v32 >> 30;
-                    c = v32 & M32;
-                }
-                if (flag == 0) continue;
-                excl[j] += c;
-                if (flag == 2 || t[j] == 0) {
-                    done[j] = true;
-                    --left;
-                } else {
-                    --t[j];
-                }
-            }
-            if (left > 0 && ++polls > kSpinLimit) {
-                atomicOr(a.status, ST_TIMEOUT);
-                break;
-            }
-            if (left > 0 && (polls & 1023u) == 0 && ld_relaxed(a.status) != 0) break;
-        }
-        const unsigned long long* boff = a.counts + (size_t)pass * bins;
-#pragma unroll
-        for (int j = 0; j < PER_MAX; ++j) {
+            cnt[j] = 0;
             const int b = b0 + j;
             if (j < per && b < bins) {
-                if (tile > 0) {
-                    const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
-                    if (a.lb64)
-                        st_relaxed((uint64_t*)a.lookback + slot, FP64 | (excl[j] + cnt[j]));
-                    else
-                        st_relaxed((uint32_t*)a.lookback + slot, FP32 | (uint32_t)(excl[j] + cnt[j]));
+                uint32_t s = 0;
+#pragma unroll 4
+                for (int w = 0; w < WARPS; ++w) {
+                    const uint32_t c = s_whist[w * bins + b];
+                    s_whist[w * bins + b] = (uint16_t)s;
+                    s += c;
                 }
-                s_gbase[b] = boff[b] + excl[j] - s_excl[b];
+                cnt[j] = s;
+                mysum += s;
+                const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
+                if (a.lb64)
+                    st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | s);
+                else
+                    st_relaxed((uint32_t*)a.lookback + slot, (tile == 0 ? FP32 : FA32) | s);
             }
         }
-    }
-    __syncthreads();
-
-    // ---- reorder the tile by digit in shared memory (stable)
+        {
+            uint32_t tot;
+            uint32_t ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tot);
 #pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-        const uint32_t dig = (uint32_t)((key[i] >> shift) & mask);
-        const uint32_t pos = s_excl[dig] + wh[dig] + rank[i];
-        s_keys[pos] = key[i];
-        if (PAIRS) s_vals[pos] = val[i];
-    }
-    __syncthreads();
-
-    // ---- coalesced stable scatter to the global digit buckets
-    const size_t valid = (n - base) < (size_t)TILE ? (n - base) : (size_t)TILE;
-    uint32_t* vdst = PAIRS ? sel_vdst(a, desc.dst) : nullptr;
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-        const int s = i * BLOCK + tid;
-        if ((size_t)s < valid) {
-            const U k = s_keys[s];
-            const uint32_t dig = (uint32_t)((k >> shift) & mask);
-            const size_t g = (size_t)(s_gbase[dig] + (unsigned long long)s);
-            st_stream(dst + g, desc.xout ? from_ordered(k, a.dt) : k);
-            if (PAIRS) st_stream(vdst + g, s_vals[s]);
+            for (int j = 0; j < PER_MAX; ++j) {
+                const int b = b0 + j;
+                if (j < per && b < bins) s_excl[b] = ex;
+                ex += cnt[j];
+            }
         }
-    }
-    __syncthreads();   // shared tile buffers are reused by the next tile
+        // ---- decoupled look-back for the owned digits
+        {
+            const unsigned long long* boff = a.counts + (size_t)pass * bins;
+#pragma unroll
+            for (int j = 0; j < PER_MAX; ++j) {
+                const int b = b0 + j;
+                if (j < per && b < bins) {
+                    uint64_t excl = 0;
+                    const size_t slot0 = (size_t)pass * a.ntiles * bins + b;
+                    if (tile > 0) {
+                        if (a.lb64) {
+                            excl = lookback_digit<uint64_t, 8>((const uint64_t*)a.lookback + slot0, bins,
+                                                               tile, a.status);
+                            st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
+                                       FP64 | (excl + cnt[j]));
+                        } else {
+                            excl = lookback_digit<uint32_t, 8>((const uint32_t*)a.lookback + slot0, bins,
+                                                               tile, a.status);
+                            st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
+                                       FP32 | (uint32_t)(excl + cnt[j]));
+                        }
+                    }
+                    s_gbase[b] = boff[b] + excl - s_excl[b];
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- reorder the tile by digit into the reorder buffer (stable)
+        {
+            const int valid_in = full ? TILE : (int)(n - base);
+#pragma unroll
+            for (int i = 0; i < KPT; ++i) {
+                const int s = wofs + 32 * i;
+                if (full || s < valid_in) {
+                    U k = s_keys[s];
+                    if (desc.xin) k = to_ordered(k, a.dt);
+                    const uint32_t dig = dr[i] & 0xFFFFu;
+                    const uint32_t pos = s_excl[dig] + wh[dig] + (dr[i] >> 16);
+                    s_rkeys[pos] = k;
+                    if (PAIRS) s_rvals[pos] = s_vals[s];
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- coalesced stable scatter to the global digit buckets
+        const int valid = full ? TILE : (int)(n - base);
+#pragma unroll
+        for (int i = 0; i < KPT; ++i) {
+            const int s = i * BLOCK + tid;
+            if (full || s < valid) {
+                const U k = s_rkeys[s];
+                const uint32_t dig = digit_of(k, shift, mask);
+                const size_t g = (size_t)(s_gbase[dig] + (unsigned long long)s);
+                st_stream(dst + g, desc.xout ? from_ordered(k, a.dt) : k);
+                if (PAIRS) st_stream(vdst + g, s_rvals[s]);
+            }
+        }
+        __syncthreads();   // the tile buffers are reused by later iterations
     }
 }
-
 // ---------------------------------------------------------------------------
 // K3b: result copy when the pass chain did not end in the output buffer.
 // ---------------------------------------------------------------------------

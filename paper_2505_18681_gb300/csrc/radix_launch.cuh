@@ -17,7 +17,7 @@ namespace evosort {
 template <typename U, bool PAIRS, int BLOCK, int KPT, int MAXB, int RANK>
 cudaError_t launch_onesweep_inst(size_t grid, int sms, cudaStream_t s, const RadixArgs& a, int pass) {
     auto kern = radix_onesweep<U, PAIRS, BLOCK, KPT, MAXB, RANK>;
-    const size_t smem = onesweep_smem_bytes<BLOCK, KPT, MAXB, PAIRS, U>(a.d);
+    const size_t smem = onesweep_smem_bytes(BLOCK, KPT, (int)sizeof(U), PAIRS, a.d);
     static size_t configured = 0;   // largest dynamic smem size set so far
     static int resident[16] = {0};  // resident CTAs per SM, by digit width
     if (smem > 48 * 1024 && smem > configured) {
@@ -62,6 +62,11 @@ inline bool onesweep_shape_supported(int block, int kpt) {
     EVOSORT_TILE_SHAPES(EVOSORT_CASE)
 #undef EVOSORT_CASE
     return false;
+}
+
+// True if the tile shape is compiled in and its shared memory fits a CTA.
+inline bool onesweep_config_fits(int w, bool pairs, int block, int kpt, int d) {
+    return onesweep_shape_supported(block, kpt) && onesweep_smem_bytes(block, kpt, w, pairs, d) <= kMaxDynSmem;
 }
 
 // Defined in radix32.cu / radix64.cu.

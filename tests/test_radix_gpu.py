@@ -98,15 +98,32 @@ def test_digit_widths(evo, d, dtype):
     run_pairs(evo, x, inplace=True, algo="radix", digit_bits=d)
 
 
+def tile_fits(block, kpt, w, pairs, d):
+    """Shared memory of one radix CTA: three tile buffers, per-warp digit
+    counters, digit offsets and bases, two mbarriers (<= 227 KB less 1 KB)."""
+    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * (1 << d) * 2 + (1 << d) * 12 + 16
+    return smem <= 232448 - 1024
+
+
 @pytest.mark.parametrize("shape", [(256, 8), (256, 16), (512, 8), (512, 16), (256, 24)])
 @pytest.mark.parametrize("rank", [1, 2])
 @pytest.mark.parametrize("d", [8, 11])
 def test_tile_shapes_and_ranking(evo, shape, rank, d):
+    """Every compiled tile shape and ranking variant; shapes whose tile does
+    not fit in shared memory must be rejected with ERR_INVALID."""
     block, kpt = shape
+    kw = dict(algo="radix", block_size=block, keys_per_thread=kpt, rank_mode=rank, digit_bits=d)
     for dtype in (torch.uint32, torch.int64):
+        w = 4 if dtype == torch.uint32 else 8
         x = gen("zipf" if dtype == torch.int64 else "uniform", 150_011, dtype)
-        run_keys(evo, x, algo="radix", block_size=block, keys_per_thread=kpt, rank_mode=rank, digit_bits=d)
-        run_pairs(evo, x, algo="radix", block_size=block, keys_per_thread=kpt, rank_mode=rank, digit_bits=d)
+        for pairs in (False, True):
+            runner = run_pairs if pairs else run_keys
+            if tile_fits(block, kpt, w, pairs, d):
+                runner(evo, x, **kw)
+            else:
+                with pytest.raises(evo.EvoSortError) as ei:
+                    runner(evo, x, **kw)
+                assert ei.value.status == "ERR_INVALID"
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=str)
