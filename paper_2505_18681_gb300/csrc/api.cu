@@ -201,6 +201,7 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     a.vtmp = pairs ? (uint32_t*)(base + L.off_vtmp) : nullptr;
     a.n = n;
     a.dt = dt;
+    a.map = key_map_for(dt);
     a.d = pl.digit_bits;
     a.npass = L.npass;
     a.lb64 = L.lb64;
@@ -291,6 +292,10 @@ static int resolve(const evosort_params* p, int dt, Plan* pl, std::string* err) 
     }
     if (pl->insertion_threshold < 2 || pl->insertion_threshold > 2048) {
         *err = "params.insertion_threshold must be in [2, 2048]";
+        return EVOSORT_ERR_INVALID;
+    }
+    if (pl->algo == EVOSORT_ALGO_RADIX && !onesweep_rank_supported(pl->rank_mode, pl->digit_bits)) {
+        *err = "params.rank_mode 1 (match) is compiled for digit_bits 8 only";
         return EVOSORT_ERR_INVALID;
     }
     if (pl->algo == EVOSORT_ALGO_RADIX && !onesweep_shape_supported(pl->block_size, pl->keys_per_thread)) {

@@ -46,13 +46,14 @@ struct RadixArgs {
     uint32_t* vtmp;
     size_t n;
     int dt;
+    KeyMap map;      // order-preserving key map of dt
     int d;           // digit bits
     int npass;       // ceil(8w / d)
     int lb64;        // look-back slots are 64-bit (n >= 2^30)
     size_t ntiles;   // tiles per pass
     PassDesc* desc;             // npass + 1 entries
     unsigned long long* counts; // npass << d digit counts, then exclusive offsets
-    void* lookback;             // npass * ntiles << d slots
+    void* lookback;             // slots [pass][digit][tile]
     uint32_t* tile_counter;     // npass counters
     uint32_t* status;
 };
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(512) radix_histogram(RadixArgs a) {
     const size_t gthreads = (size_t)gridDim.x * blockDim.x;
 
     auto count_key = [&](U k) {
-        k = to_ordered(k, a.dt);
+        k = map_fwd(k, a.map);
         for (int p = 0; p < a.npass; ++p) {
             const uint32_t dig = (uint32_t)((k >> (p * a.d)) & mask);
             atomicAdd(&s_h[p * bins + dig], 1u);
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(512) radix_histogram(RadixArgs a) {
         U k[V];
         memcpy(k, &v, 16);
 #pragma unroll
-        for (int j = 0; j < V; ++j) k[j] = to_ordered(k[j], a.dt);
+        for (int j = 0; j < V; ++j) k[j] = map_fwd(k[j], a.map);
         for (int p = 0; p < a.npass; ++p) {
             const int sh = p * a.d;
             uint32_t prev = (uint32_t)((k[0] >> sh) & mask);
@@ -210,15 +211,17 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
 // TMA engine copy that tile (keys, and values for pairs) into the other half
 // of a double input buffer; a third buffer receives the reordered tile.
 // ---------------------------------------------------------------------------
-template <int RANK>
-__device__ __forceinline__ uint32_t warp_peers(uint32_t dig, int d) {
+template <int RANK, int D>
+__device__ __forceinline__ uint32_t warp_peers(uint32_t dig) {
     if (RANK == 1) {
         return __match_any_sync(0xffffffffu, dig);
     } else {
         uint32_t peers = 0xffffffffu;
-        for (int bit = 0; bit < d; ++bit) {
-            const uint32_t b = __ballot_sync(0xffffffffu, (dig >> bit) & 1u);
-            peers &= ((dig >> bit) & 1u) ? b : ~b;
+#pragma unroll
+        for (int bit = 0; bit < D; ++bit) {
+            const bool set = (dig >> bit) & 1u;
+            const uint32_t b = __ballot_sync(0xffffffffu, set);
+            peers &= set ? b : ~b;
         }
         return peers;
     }
@@ -226,74 +229,100 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t dig, int d) {
 
 // Dynamic shared memory of one onesweep CTA: three tile buffers (two TMA
 // input buffers, one reorder buffer), per-warp digit counters, the tile's
-// digit offsets and global bases, two mbarriers.
+// digit offsets, counts and global bases, two mbarriers.
 __host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d) {
     return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * ((size_t)1 << d) * 2 +
-           ((size_t)1 << d) * 4 + ((size_t)1 << d) * 8 + 16;
+           ((size_t)1 << d) * 16 + 16;
 }
 // Largest dynamic shared memory a CTA may use on sm_100-class GPUs (227 KB),
 // less room for the kernel's static shared variables.
 constexpr size_t kMaxDynSmem = 232448 - 1024;
 
-// Decoupled look-back for one digit: sums the counts of the preceding tiles
-// back to the nearest inclusive prefix.  LBW slots are read per L2 round trip.
-template <typename S, int LBW>
-__device__ __forceinline__ uint64_t lookback_digit(const S* slot0, size_t stride, long long tile,
-                                                   uint32_t* status) {
-    constexpr int FB = sizeof(S) * 8 - 2;   // flag bits: 01 aggregate, 10 inclusive prefix
+// Decoupled look-back, warp-cooperative.  The slots of one digit are stored
+// with tiles contiguous, so lane L of a warp reads the slot of tile t0 - L in
+// one coalesced load: 32 predecessors per L2 round trip.  A slot holds a flag
+// in its top two bits (01 aggregate of that tile, 10 inclusive prefix up to
+// and including it, 00 not yet published) and a count below.  The walk stops
+// at the nearest inclusive prefix; it waits (bounded) on unpublished slots.
+// NB bins are resolved together so their loads overlap.
+template <typename S, int NB>
+__device__ __forceinline__ void warp_lookback(const S* row0, size_t stride, int tile, S (&excl)[NB], int nvalid,
+                                              uint32_t* status) {
+    constexpr int FB = sizeof(S) * 8 - 2;
     const S cmask = ((S)1 << FB) - 1;
-    uint64_t excl = 0;
-    long long t = tile - 1;
+    const int lane = threadIdx.x & 31;
+    int t0[NB];
+    uint32_t done = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        excl[j] = 0;
+        t0[j] = tile - 1;
+        if (j >= nvalid) done |= 1u << j;
+    }
+    const uint32_t all = (NB >= 32) ? 0xffffffffu : ((1u << NB) - 1);
     uint32_t polls = 0;
-    while (t >= 0) {
-        S v[LBW];
+    while (done != all) {
+        S v[NB];
 #pragma unroll
-        for (int k = 0; k < LBW; ++k)
-            v[k] = (t - k >= 0) ? ld_relaxed(slot0 + (size_t)(t - k) * stride) : ((S)2 << FB);
-        int adv = 0;
-        bool fin = false, blocked = false;
+        for (int j = 0; j < NB; ++j) {
+            const int t = t0[j] - lane;
+            v[j] = (!((done >> j) & 1u) && t >= 0) ? ld_relaxed(row0 + j * stride + t) : ((S)2 << FB);
+        }
+        bool waited = false;
 #pragma unroll
-        for (int k = 0; k < LBW; ++k) {
-            if (!fin && !blocked) {
-                const uint32_t f = (uint32_t)(v[k] >> FB);
-                if (f == 0) {
-                    blocked = true;
-                } else {
-                    excl += (uint64_t)(v[k] & cmask);
-                    ++adv;
-                    if (f == 2) fin = true;
-                }
+        for (int j = 0; j < NB; ++j) {
+            if ((done >> j) & 1u) continue;
+            const uint32_t f = (uint32_t)(v[j] >> FB);
+            const uint32_t pm = __ballot_sync(0xffffffffu, f == 2u);
+            const uint32_t xm = __ballot_sync(0xffffffffu, f == 0u);
+            const uint32_t upto = pm ? (((pm & (0u - pm)) << 1) - 1u) : 0xffffffffu;
+            const uint32_t blocked = xm & upto;
+            const uint32_t take = blocked ? ((blocked & (0u - blocked)) - 1u) : upto;
+            S c = ((take >> lane) & 1u) ? (v[j] & cmask) : (S)0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            excl[j] += c;
+            if (blocked) {
+                t0[j] -= __popc(take);
+                waited = true;
+            } else if (pm) {
+                done |= 1u << j;
+            } else {
+                t0[j] -= 32;
             }
         }
-        if (fin) break;
-        t -= adv;
-        if (blocked) {
+        if (waited) {
             if (++polls > kSpinLimit) {
                 atomicOr(status, ST_TIMEOUT);
                 break;
             }
             if ((polls & 255u) == 0 && ld_relaxed(status) != 0) break;
-            __nanosleep(32);
+            __nanosleep(64);
         }
     }
-    return excl;
 }
 
-template <typename U, bool PAIRS, int BLOCK, int KPT, int MAXB, int RANK>
-__global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(RadixArgs a, int pass) {
+// CTAs per SM the register budget is tuned for: about 40 registers plus one
+// per key of the thread.
+constexpr int onesweep_min_blocks(int block, int kpt) {
+    return 65536 / (block * (kpt + 40)) < 1 ? 1 : (65536 / (block * (kpt + 40)) > 4 ? 4 : 65536 / (block * (kpt + 40)));
+}
+
+template <typename U, bool PAIRS, int BLOCK, int KPT, int D, int RANK>
+__global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_onesweep(RadixArgs a, int pass) {
     constexpr int WARPS = BLOCK / 32;
     constexpr int TILE = BLOCK * KPT;
-    constexpr int PER_MAX = ((1 << MAXB) + BLOCK - 1) / BLOCK;
+    constexpr int PER_MAX = ((1 << D) + BLOCK - 1) / BLOCK;
     constexpr size_t KB = (size_t)TILE * sizeof(U);
     constexpr size_t VB = PAIRS ? (size_t)TILE * 4 : 0;
     const PassDesc desc = a.desc[pass];
     if (!desc.active) return;
 
-    const int d = a.d;
-    const int bins = 1 << d;
-    const int shift = pass * d;
-    const uint32_t mask = (uint32_t)(bins - 1);
+    constexpr int bins = 1 << D;
+    const int shift = pass * D;
+    constexpr uint32_t mask = (uint32_t)(bins - 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const KeyMap map = a.map;
 
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* bufs = smem;   // two input tile buffers of KB + VB bytes
@@ -301,7 +330,8 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
     uint32_t* s_rvals = (uint32_t*)(smem + 2 * (KB + VB) + KB);
     uint16_t* s_whist = (uint16_t*)(smem + 3 * (KB + VB));
     uint32_t* s_excl = (uint32_t*)(s_whist + WARPS * bins);
-    unsigned long long* s_gbase = (unsigned long long*)(s_excl + bins);
+    uint32_t* s_cnt = s_excl + bins;
+    unsigned long long* s_gbase = (unsigned long long*)(s_cnt + bins);
     uint64_t* s_bar = (uint64_t*)(s_gbase + bins);
     __shared__ uint32_t s_tile[2];
     __shared__ uint32_t s_scr[WARPS + 1];
@@ -369,7 +399,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
 #pragma unroll
             for (int i = 0; i < KPT; ++i) {
                 U k = s_keys[wofs + 32 * i];
-                if (desc.xin) k = to_ordered(k, a.dt);
+                if (desc.xin) k = map_fwd(k, map);
                 dr[i] = digit_of(k, shift, mask);
             }
         } else {
@@ -381,7 +411,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
                     const U raw = ld_stream(src + idx);
                     s_keys[wofs + 32 * i] = raw;
                     if (PAIRS) s_vals[wofs + 32 * i] = ld_stream(vsrc + idx);
-                    k = desc.xin ? to_ordered(raw, a.dt) : raw;
+                    k = desc.xin ? map_fwd(raw, map) : raw;
                 }
                 dr[i] = digit_of(k, shift, mask);
             }
@@ -393,7 +423,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
 #pragma unroll
         for (int i = 0; i < KPT; ++i) {
             const uint32_t dig = dr[i];
-            const uint32_t peers = warp_peers<RANK>(dig, d);
+            const uint32_t peers = warp_peers<RANK, D>(dig);
             const int leader = 31 - __clz(peers);
             uint32_t old = 0;
             if (lane == leader) {
@@ -406,8 +436,9 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
         }
         __syncthreads();
 
-        // ---- tile digit counts; warp counts -> exclusive prefix over warps
-        const int per = (bins + BLOCK - 1) / BLOCK;
+        // ---- tile digit counts; warp counts -> exclusive prefix over warps;
+        // publish each digit's tile aggregate (tile 0: its inclusive prefix)
+        constexpr int per = PER_MAX;
         const int b0 = tid * per;
         uint32_t cnt[PER_MAX];
         uint32_t mysum = 0;
@@ -415,7 +446,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
         for (int j = 0; j < PER_MAX; ++j) {
             cnt[j] = 0;
             const int b = b0 + j;
-            if (j < per && b < bins) {
+            if (b < bins) {
                 uint32_t s = 0;
 #pragma unroll 4
                 for (int w = 0; w < WARPS; ++w) {
@@ -425,7 +456,8 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
                 }
                 cnt[j] = s;
                 mysum += s;
-                const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
+                s_cnt[b] = s;
+                const size_t slot = ((size_t)pass * bins + b) * a.ntiles + tile;
                 if (a.lb64)
                     st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | s);
                 else
@@ -438,33 +470,44 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
 #pragma unroll
             for (int j = 0; j < PER_MAX; ++j) {
                 const int b = b0 + j;
-                if (j < per && b < bins) s_excl[b] = ex;
+                if (b < bins) s_excl[b] = ex;
                 ex += cnt[j];
             }
         }
-        // ---- decoupled look-back for the owned digits
+        __syncthreads();
+        // ---- decoupled look-back: warp w resolves digits w, w + WARPS, ...
         {
             const unsigned long long* boff = a.counts + (size_t)pass * bins;
+            constexpr int NB = 8;
+            for (int bb = warp * NB; bb < bins; bb += WARPS * NB) {
+                const int nvalid = bins - bb < NB ? bins - bb : NB;
+                const size_t row0 = ((size_t)pass * bins + bb) * a.ntiles;
+                if (a.lb64) {
+                    uint64_t* slots = (uint64_t*)a.lookback + row0;
+                    uint64_t ex[NB];
+                    if (tile > 0) warp_lookback<uint64_t, NB>(slots, a.ntiles, (int)tile, ex, nvalid, a.status);
 #pragma unroll
-            for (int j = 0; j < PER_MAX; ++j) {
-                const int b = b0 + j;
-                if (j < per && b < bins) {
-                    uint64_t excl = 0;
-                    const size_t slot0 = (size_t)pass * a.ntiles * bins + b;
-                    if (tile > 0) {
-                        if (a.lb64) {
-                            excl = lookback_digit<uint64_t, 8>((const uint64_t*)a.lookback + slot0, bins,
-                                                               tile, a.status);
-                            st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
-                                       FP64 | (excl + cnt[j]));
-                        } else {
-                            excl = lookback_digit<uint32_t, 8>((const uint32_t*)a.lookback + slot0, bins,
-                                                               tile, a.status);
-                            st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
-                                       FP32 | (uint32_t)(excl + cnt[j]));
+                    for (int j = 0; j < NB; ++j) {
+                        if (tile == 0) ex[j] = 0;
+                        if (j < nvalid && lane == j) {
+                            const int b = bb + j;
+                            if (tile > 0) st_relaxed(slots + j * a.ntiles + tile, FP64 | (ex[j] + s_cnt[b]));
+                            s_gbase[b] = boff[b] + ex[j] - s_excl[b];
                         }
                     }
-                    s_gbase[b] = boff[b] + excl - s_excl[b];
+                } else {
+                    uint32_t* slots = (uint32_t*)a.lookback + row0;
+                    uint32_t ex[NB];
+                    if (tile > 0) warp_lookback<uint32_t, NB>(slots, a.ntiles, (int)tile, ex, nvalid, a.status);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) {
+                        if (tile == 0) ex[j] = 0;
+                        if (j < nvalid && lane == j) {
+                            const int b = bb + j;
+                            if (tile > 0) st_relaxed(slots + j * a.ntiles + tile, FP32 | (ex[j] + s_cnt[b]));
+                            s_gbase[b] = boff[b] + ex[j] - s_excl[b];
+                        }
+                    }
                 }
             }
         }
@@ -478,7 +521,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
                 const int s = wofs + 32 * i;
                 if (full || s < valid_in) {
                     U k = s_keys[s];
-                    if (desc.xin) k = to_ordered(k, a.dt);
+                    if (desc.xin) k = map_fwd(k, map);
                     const uint32_t dig = dr[i] & 0xFFFFu;
                     const uint32_t pos = s_excl[dig] + wh[dig] + (dr[i] >> 16);
                     s_rkeys[pos] = k;
@@ -497,7 +540,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 512 ? 2 : 4)) radix_onesweep(
                 const U k = s_rkeys[s];
                 const uint32_t dig = digit_of(k, shift, mask);
                 const size_t g = (size_t)(s_gbase[dig] + (unsigned long long)s);
-                st_stream(dst + g, desc.xout ? from_ordered(k, a.dt) : k);
+                st_stream(dst + g, desc.xout ? map_inv(k, map) : k);
                 if (PAIRS) st_stream(vdst + g, s_rvals[s]);
             }
         }

@@ -1,13 +1,19 @@
-// Onesweep pass kernels for 64-bit keys (int64, uint64, float64), plus the
-// histogram, scan/plan and fixup kernels of both key widths.
+// Histogram, scan/plan and fixup kernels of both key widths, and the
+// dispatch to the per-width onesweep translation units.
 #include "radix_launch.cuh"
 
 namespace evosort {
 
+cudaError_t launch_onesweep_u32(bool pairs, int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
+                                const RadixArgs& a, int pass) {
+    return pairs ? launch_onesweep_u32_pairs(block, kpt, rank, grid, sms, s, a, pass)
+                 : launch_onesweep_u32_keys(block, kpt, rank, grid, sms, s, a, pass);
+}
+
 cudaError_t launch_onesweep_u64(bool pairs, int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
                                 const RadixArgs& a, int pass) {
-    return pairs ? launch_onesweep_shape<uint64_t, true>(block, kpt, rank, grid, sms, s, a, pass)
-                 : launch_onesweep_shape<uint64_t, false>(block, kpt, rank, grid, sms, s, a, pass);
+    return pairs ? launch_onesweep_u64_pairs(block, kpt, rank, grid, sms, s, a, pass)
+                 : launch_onesweep_u64_keys(block, kpt, rank, grid, sms, s, a, pass);
 }
 
 // which: 0 = histogram, 1 = scan/plan, 2 = fixup

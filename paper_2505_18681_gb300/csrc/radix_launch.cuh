@@ -1,5 +1,5 @@
-// Instantiation table of the onesweep pass kernel.  Each key width gets its own
-// translation unit (radix32.cu, radix64.cu) so the two compile in parallel.
+// Instantiation table of the onesweep pass kernel.  Each (key width, pairs)
+// combination has its own translation unit so they compile in parallel.
 #pragma once
 
 #include "radix.cuh"
@@ -10,47 +10,58 @@ namespace evosort {
 #define EVOSORT_TILE_SHAPES(X) \
     X(256, 8)                  \
     X(256, 16)                 \
-    X(512, 8)                  \
+    X(256, 32)                 \
     X(512, 16)                 \
-    X(256, 24)
+    X(512, 32)
 
-template <typename U, bool PAIRS, int BLOCK, int KPT, int MAXB, int RANK>
+template <typename U, bool PAIRS, int BLOCK, int KPT, int D, int RANK>
 cudaError_t launch_onesweep_inst(size_t grid, int sms, cudaStream_t s, const RadixArgs& a, int pass) {
-    auto kern = radix_onesweep<U, PAIRS, BLOCK, KPT, MAXB, RANK>;
-    const size_t smem = onesweep_smem_bytes(BLOCK, KPT, (int)sizeof(U), PAIRS, a.d);
-    static size_t configured = 0;   // largest dynamic smem size set so far
-    static int resident[16] = {0};  // resident CTAs per SM, by digit width
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = radix_onesweep<U, PAIRS, BLOCK, KPT, D, RANK>;
+    const size_t smem = onesweep_smem_bytes(BLOCK, KPT, (int)sizeof(U), PAIRS, D);
+    static int resident = 0;   // resident CTAs per SM
+    if (resident == 0) {
+        cudaError_t e = cudaSuccess;
+        if (smem > 48 * 1024)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
-    }
-    if (resident[a.d] == 0) {
         int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BLOCK, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BLOCK, smem);
         if (e != cudaSuccess) return e;
-        resident[a.d] = nb > 0 ? nb : 1;
+        resident = nb > 0 ? nb : 1;
     }
     // persistent grid: every SM full, never more CTAs than tiles
-    size_t g = (size_t)sms * resident[a.d];
+    size_t g = (size_t)sms * resident;
     if (g > grid) g = grid;
     if (g < 1) g = 1;
     kern<<<(unsigned)g, BLOCK, smem, s>>>(a, pass);
     return cudaGetLastError();
 }
 
+// Digit widths 4..11 with per-bit ballot ranking; match.any ranking for d = 8.
+template <typename U, bool PAIRS, int B, int K>
+cudaError_t launch_onesweep_d(int rank, size_t grid, int sms, cudaStream_t s, const RadixArgs& a, int pass) {
+    if (rank == 1) {
+        if (a.d == 8) return launch_onesweep_inst<U, PAIRS, B, K, 8, 1>(grid, sms, s, a, pass);
+        return cudaErrorInvalidConfiguration;
+    }
+    switch (a.d) {
+        case 4: return launch_onesweep_inst<U, PAIRS, B, K, 4, 2>(grid, sms, s, a, pass);
+        case 5: return launch_onesweep_inst<U, PAIRS, B, K, 5, 2>(grid, sms, s, a, pass);
+        case 6: return launch_onesweep_inst<U, PAIRS, B, K, 6, 2>(grid, sms, s, a, pass);
+        case 7: return launch_onesweep_inst<U, PAIRS, B, K, 7, 2>(grid, sms, s, a, pass);
+        case 8: return launch_onesweep_inst<U, PAIRS, B, K, 8, 2>(grid, sms, s, a, pass);
+        case 9: return launch_onesweep_inst<U, PAIRS, B, K, 9, 2>(grid, sms, s, a, pass);
+        case 10: return launch_onesweep_inst<U, PAIRS, B, K, 10, 2>(grid, sms, s, a, pass);
+        case 11: return launch_onesweep_inst<U, PAIRS, B, K, 11, 2>(grid, sms, s, a, pass);
+    }
+    return cudaErrorInvalidConfiguration;
+}
+
 template <typename U, bool PAIRS>
 cudaError_t launch_onesweep_shape(int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
                                   const RadixArgs& a, int pass) {
-    const bool wide = a.d > 8;
-#define EVOSORT_CASE(B, K)                                                                        \
-    if (block == B && kpt == K) {                                                                 \
-        if (wide)                                                                                 \
-            return rank == 2 ? launch_onesweep_inst<U, PAIRS, B, K, 11, 2>(grid, sms, s, a, pass)      \
-                             : launch_onesweep_inst<U, PAIRS, B, K, 11, 1>(grid, sms, s, a, pass);     \
-        return rank == 2 ? launch_onesweep_inst<U, PAIRS, B, K, 8, 2>(grid, sms, s, a, pass)           \
-                         : launch_onesweep_inst<U, PAIRS, B, K, 8, 1>(grid, sms, s, a, pass);          \
-    }
+#define EVOSORT_CASE(B, K) \
+    if (block == B && kpt == K) return launch_onesweep_d<U, PAIRS, B, K>(rank, grid, sms, s, a, pass);
     EVOSORT_TILE_SHAPES(EVOSORT_CASE)
 #undef EVOSORT_CASE
     return cudaErrorInvalidConfiguration;
@@ -69,7 +80,19 @@ inline bool onesweep_config_fits(int w, bool pairs, int block, int kpt, int d) {
     return onesweep_shape_supported(block, kpt) && onesweep_smem_bytes(block, kpt, w, pairs, d) <= kMaxDynSmem;
 }
 
-// Defined in radix32.cu / radix64.cu.
+// match.any ranking is compiled for 8-bit digits only.
+inline bool onesweep_rank_supported(int rank, int d) { return rank == 2 || (rank == 1 && d == 8); }
+
+// Defined in radix32k.cu, radix32p.cu, radix64k.cu, radix64p.cu.
+cudaError_t launch_onesweep_u32_keys(int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
+                                     const RadixArgs& a, int pass);
+cudaError_t launch_onesweep_u32_pairs(int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
+                                      const RadixArgs& a, int pass);
+cudaError_t launch_onesweep_u64_keys(int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
+                                     const RadixArgs& a, int pass);
+cudaError_t launch_onesweep_u64_pairs(int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
+                                      const RadixArgs& a, int pass);
+// Defined in radix_aux.cu.
 cudaError_t launch_onesweep_u32(bool pairs, int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
                                 const RadixArgs& a, int pass);
 cudaError_t launch_onesweep_u64(bool pairs, int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
