@@ -83,7 +83,10 @@ typedef struct {
     int block_size;           /* threads per CTA: 256 or 512 */
     int insertion_threshold;  /* mergesort base-run length T_insertion, 2..2048
                                  (default 32; Section 4.2 bounds) */
-    int rank_mode;            /* radix tile ranking: 1 = warp match, 2 = ballot */
+    int rank_mode;            /* radix tile ranking (how a warp finds lanes with
+                                 equal digits): 1 = match.any (d = 8 only),
+                                 2 = one ballot per digit bit (any d),
+                                 3 = shared-memory match masks (d <= 8; default) */
     void* stream;             /* cudaStream_t */
     void* workspace;          /* optional caller scratch, device, 256-B aligned */
     size_t workspace_bytes;

@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/evosort.h"
+#include "evosort.h"
 #include "api_internal.h"
 #include "radix_launch.cuh"
 
@@ -265,7 +265,7 @@ static void defaults_for(int w, Plan* pl) {
     pl->block_size = 256;
     pl->keys_per_thread = w == 4 ? 16 : 8;
     pl->insertion_threshold = 32;
-    pl->rank_mode = 2;
+    pl->rank_mode = 3;
 }
 
 static int resolve(const evosort_params* p, int dt, Plan* pl, std::string* err) {
@@ -286,8 +286,8 @@ static int resolve(const evosort_params* p, int dt, Plan* pl, std::string* err) 
         *err = "params.digit_bits must be in [4, 11]";
         return EVOSORT_ERR_INVALID;
     }
-    if (pl->rank_mode != 1 && pl->rank_mode != 2) {
-        *err = "params.rank_mode must be 1 or 2";
+    if (pl->rank_mode < 1 || pl->rank_mode > 3) {
+        *err = "params.rank_mode must be 1, 2 or 3";
         return EVOSORT_ERR_INVALID;
     }
     if (pl->insertion_threshold < 2 || pl->insertion_threshold > 2048) {
@@ -295,7 +295,7 @@ static int resolve(const evosort_params* p, int dt, Plan* pl, std::string* err) 
         return EVOSORT_ERR_INVALID;
     }
     if (pl->algo == EVOSORT_ALGO_RADIX && !onesweep_rank_supported(pl->rank_mode, pl->digit_bits)) {
-        *err = "params.rank_mode 1 (match) is compiled for digit_bits 8 only";
+        *err = "params.rank_mode: 1 (match.any) needs digit_bits 8, 3 (match masks) needs digit_bits <= 8";
         return EVOSORT_ERR_INVALID;
     }
     if (pl->algo == EVOSORT_ALGO_RADIX && !onesweep_shape_supported(pl->block_size, pl->keys_per_thread)) {
@@ -341,7 +341,7 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     int rc = resolve(p, dt, &pl, &err);
     if (rc) return finish(rc, err);
     if (pl.algo == EVOSORT_ALGO_RADIX &&
-        !onesweep_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits))
+        !onesweep_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits, pl.rank_mode))
         return finish(EVOSORT_ERR_INVALID, "radix tile does not fit in shared memory (block_size x "
                                            "keys_per_thread too large for this key width and digit width)");
     cudaStream_t s = p ? (cudaStream_t)p->stream : nullptr;

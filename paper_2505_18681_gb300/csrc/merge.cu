@@ -1,5 +1,5 @@
 // Bottom-up mergesort (Algorithm 3 of the paper).
-#include "../../include/evosort.h"
+#include "evosort.h"
 #include "api_internal.h"
 #include "common.cuh"
 

@@ -53,7 +53,7 @@ struct RadixArgs {
     size_t ntiles;   // tiles per pass
     PassDesc* desc;             // npass + 1 entries
     unsigned long long* counts; // npass << d digit counts, then exclusive offsets
-    void* lookback;             // slots [pass][digit][tile]
+    void* lookback;             // slots [pass][tile][digit]
     uint32_t* tile_counter;     // npass counters
     uint32_t* status;
 };
@@ -203,7 +203,9 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
 
 // ---------------------------------------------------------------------------
 // K3: one onesweep pass.  RANK selects how a warp finds the lanes that share
-// a digit: 1 = match.any, 2 = one ballot per digit bit.
+// a digit: 1 = match.any, 2 = one ballot per digit bit, 3 = shared-memory
+// match masks built with atomicOr (fewest instructions; serialises when many
+// lanes share a digit, as in sorted or low-entropy input).
 //
 // Persistent CTAs take tiles in order from an atomic counter, so every tile's
 // predecessors are held by running CTAs and the look-back always progresses.
@@ -229,77 +231,58 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t dig) {
 
 // Dynamic shared memory of one onesweep CTA: three tile buffers (two TMA
 // input buffers, one reorder buffer), per-warp digit counters, the tile's
-// digit offsets, counts and global bases, two mbarriers.
-__host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d) {
+// digit offsets and global bases, two mbarriers, and for rank mode 3 the
+// per-warp match masks.
+__host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d, int rank) {
     return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * ((size_t)1 << d) * 2 +
-           ((size_t)1 << d) * 16 + 16;
+           ((size_t)1 << d) * 12 + 16 + (rank == 3 ? (size_t)(block / 32) * ((size_t)1 << d) * 4 : 0);
 }
 // Largest dynamic shared memory a CTA may use on sm_100-class GPUs (227 KB),
 // less room for the kernel's static shared variables.
 constexpr size_t kMaxDynSmem = 232448 - 1024;
 
-// Decoupled look-back, warp-cooperative.  The slots of one digit are stored
-// with tiles contiguous, so lane L of a warp reads the slot of tile t0 - L in
-// one coalesced load: 32 predecessors per L2 round trip.  A slot holds a flag
-// in its top two bits (01 aggregate of that tile, 10 inclusive prefix up to
-// and including it, 00 not yet published) and a count below.  The walk stops
-// at the nearest inclusive prefix; it waits (bounded) on unpublished slots.
-// NB bins are resolved together so their loads overlap.
-template <typename S, int NB>
-__device__ __forceinline__ void warp_lookback(const S* row0, size_t stride, int tile, S (&excl)[NB], int nvalid,
-                                              uint32_t* status) {
-    constexpr int FB = sizeof(S) * 8 - 2;
+// Decoupled look-back for one digit: sums the counts of the preceding tiles
+// back to the nearest inclusive prefix.  LBW slots are read per L2 round trip.
+template <typename S, int LBW>
+__device__ __forceinline__ uint64_t lookback_digit(const S* slot0, size_t stride, long long tile,
+                                                   uint32_t* status) {
+    constexpr int FB = sizeof(S) * 8 - 2;   // flag bits: 01 aggregate, 10 inclusive prefix
     const S cmask = ((S)1 << FB) - 1;
-    const int lane = threadIdx.x & 31;
-    int t0[NB];
-    uint32_t done = 0;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        excl[j] = 0;
-        t0[j] = tile - 1;
-        if (j >= nvalid) done |= 1u << j;
-    }
-    const uint32_t all = (NB >= 32) ? 0xffffffffu : ((1u << NB) - 1);
+    uint64_t excl = 0;
+    long long t = tile - 1;
     uint32_t polls = 0;
-    while (done != all) {
-        S v[NB];
+    while (t >= 0) {
+        S v[LBW];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const int t = t0[j] - lane;
-            v[j] = (!((done >> j) & 1u) && t >= 0) ? ld_relaxed(row0 + j * stride + t) : ((S)2 << FB);
-        }
-        bool waited = false;
+        for (int k = 0; k < LBW; ++k)
+            v[k] = (t - k >= 0) ? ld_relaxed(slot0 + (size_t)(t - k) * stride) : ((S)2 << FB);
+        int adv = 0;
+        bool fin = false, blocked = false;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            if ((done >> j) & 1u) continue;
-            const uint32_t f = (uint32_t)(v[j] >> FB);
-            const uint32_t pm = __ballot_sync(0xffffffffu, f == 2u);
-            const uint32_t xm = __ballot_sync(0xffffffffu, f == 0u);
-            const uint32_t upto = pm ? (((pm & (0u - pm)) << 1) - 1u) : 0xffffffffu;
-            const uint32_t blocked = xm & upto;
-            const uint32_t take = blocked ? ((blocked & (0u - blocked)) - 1u) : upto;
-            S c = ((take >> lane) & 1u) ? (v[j] & cmask) : (S)0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-            excl[j] += c;
-            if (blocked) {
-                t0[j] -= __popc(take);
-                waited = true;
-            } else if (pm) {
-                done |= 1u << j;
-            } else {
-                t0[j] -= 32;
+        for (int k = 0; k < LBW; ++k) {
+            if (!fin && !blocked) {
+                const uint32_t f = (uint32_t)(v[k] >> FB);
+                if (f == 0) {
+                    blocked = true;
+                } else {
+                    excl += (uint64_t)(v[k] & cmask);
+                    ++adv;
+                    if (f == 2) fin = true;
+                }
             }
         }
-        if (waited) {
+        if (fin) break;
+        t -= adv;
+        if (blocked) {
             if (++polls > kSpinLimit) {
                 atomicOr(status, ST_TIMEOUT);
                 break;
             }
             if ((polls & 255u) == 0 && ld_relaxed(status) != 0) break;
-            __nanosleep(64);
+            __nanosleep(32);
         }
     }
+    return excl;
 }
 
 // CTAs per SM the register budget is tuned for: about 40 registers plus one
@@ -330,9 +313,9 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     uint32_t* s_rvals = (uint32_t*)(smem + 2 * (KB + VB) + KB);
     uint16_t* s_whist = (uint16_t*)(smem + 3 * (KB + VB));
     uint32_t* s_excl = (uint32_t*)(s_whist + WARPS * bins);
-    uint32_t* s_cnt = s_excl + bins;
-    unsigned long long* s_gbase = (unsigned long long*)(s_cnt + bins);
+    unsigned long long* s_gbase = (unsigned long long*)(s_excl + bins);
     uint64_t* s_bar = (uint64_t*)(s_gbase + bins);
+    uint32_t* s_match = (uint32_t*)(s_bar + 2);   // RANK 3: WARPS x bins match masks
     __shared__ uint32_t s_tile[2];
     __shared__ uint32_t s_scr[WARPS + 1];
 
@@ -344,6 +327,8 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     const bool use_tma = (((uintptr_t)src & 15) == 0) && (!PAIRS || (((uintptr_t)vsrc & 15) == 0));
     const size_t full_tiles = n / TILE;
 
+    if (RANK == 3)
+        for (int i = tid; i < WARPS * bins; i += BLOCK) s_match[i] = 0u;
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
@@ -384,6 +369,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         U* s_keys = (U*)kb;
         uint32_t* s_vals = (uint32_t*)(kb + KB);
         uint16_t* wh = s_whist + warp * bins;
+        uint32_t* wm = s_match + warp * bins;
         for (int i = lane; i < bins / 2; i += 32) ((uint32_t*)wh)[i] = 0;
 
         // ---- keys of the tile, warp-striped (warp w owns a contiguous run of
@@ -423,12 +409,23 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
 #pragma unroll
         for (int i = 0; i < KPT; ++i) {
             const uint32_t dig = dr[i];
-            const uint32_t peers = warp_peers<RANK, D>(dig);
+            uint32_t peers;
+            if (RANK == 3) {
+                // peers from per-warp shared match masks: every lane ORs its bit
+                // into its digit's word and reads the word back
+                atomicOr(&wm[dig], 1u << lane);
+                __syncwarp();
+                peers = wm[dig];
+                __syncwarp();
+            } else {
+                peers = warp_peers<RANK, D>(dig);
+            }
             const int leader = 31 - __clz(peers);
             uint32_t old = 0;
             if (lane == leader) {
                 old = wh[dig];
                 wh[dig] = (uint16_t)(old + __popc(peers));
+                if (RANK == 3) wm[dig] = 0u;
             }
             old = __shfl_sync(0xffffffffu, old, leader);
             dr[i] = dig | ((old + __popc(peers & lt)) << 16);
@@ -436,8 +433,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         }
         __syncthreads();
 
-        // ---- tile digit counts; warp counts -> exclusive prefix over warps;
-        // publish each digit's tile aggregate (tile 0: its inclusive prefix)
+        // ---- tile digit counts; warp counts -> exclusive prefix over warps
         constexpr int per = PER_MAX;
         const int b0 = tid * per;
         uint32_t cnt[PER_MAX];
@@ -446,7 +442,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         for (int j = 0; j < PER_MAX; ++j) {
             cnt[j] = 0;
             const int b = b0 + j;
-            if (b < bins) {
+            if (j < per && b < bins) {
                 uint32_t s = 0;
 #pragma unroll 4
                 for (int w = 0; w < WARPS; ++w) {
@@ -456,8 +452,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                 }
                 cnt[j] = s;
                 mysum += s;
-                s_cnt[b] = s;
-                const size_t slot = ((size_t)pass * bins + b) * a.ntiles + tile;
+                const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
                 if (a.lb64)
                     st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | s);
                 else
@@ -470,44 +465,33 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
 #pragma unroll
             for (int j = 0; j < PER_MAX; ++j) {
                 const int b = b0 + j;
-                if (b < bins) s_excl[b] = ex;
+                if (j < per && b < bins) s_excl[b] = ex;
                 ex += cnt[j];
             }
         }
-        __syncthreads();
-        // ---- decoupled look-back: warp w resolves digits w, w + WARPS, ...
+        // ---- decoupled look-back for the owned digits
         {
             const unsigned long long* boff = a.counts + (size_t)pass * bins;
-            constexpr int NB = 8;
-            for (int bb = warp * NB; bb < bins; bb += WARPS * NB) {
-                const int nvalid = bins - bb < NB ? bins - bb : NB;
-                const size_t row0 = ((size_t)pass * bins + bb) * a.ntiles;
-                if (a.lb64) {
-                    uint64_t* slots = (uint64_t*)a.lookback + row0;
-                    uint64_t ex[NB];
-                    if (tile > 0) warp_lookback<uint64_t, NB>(slots, a.ntiles, (int)tile, ex, nvalid, a.status);
 #pragma unroll
-                    for (int j = 0; j < NB; ++j) {
-                        if (tile == 0) ex[j] = 0;
-                        if (j < nvalid && lane == j) {
-                            const int b = bb + j;
-                            if (tile > 0) st_relaxed(slots + j * a.ntiles + tile, FP64 | (ex[j] + s_cnt[b]));
-                            s_gbase[b] = boff[b] + ex[j] - s_excl[b];
+            for (int j = 0; j < PER_MAX; ++j) {
+                const int b = b0 + j;
+                if (j < per && b < bins) {
+                    uint64_t excl = 0;
+                    const size_t slot0 = (size_t)pass * a.ntiles * bins + b;
+                    if (tile > 0) {
+                        if (a.lb64) {
+                            excl = lookback_digit<uint64_t, 8>((const uint64_t*)a.lookback + slot0, bins,
+                                                               tile, a.status);
+                            st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
+                                       FP64 | (excl + cnt[j]));
+                        } else {
+                            excl = lookback_digit<uint32_t, 8>((const uint32_t*)a.lookback + slot0, bins,
+                                                               tile, a.status);
+                            st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
+                                       FP32 | (uint32_t)(excl + cnt[j]));
                         }
                     }
-                } else {
-                    uint32_t* slots = (uint32_t*)a.lookback + row0;
-                    uint32_t ex[NB];
-                    if (tile > 0) warp_lookback<uint32_t, NB>(slots, a.ntiles, (int)tile, ex, nvalid, a.status);
-#pragma unroll
-                    for (int j = 0; j < NB; ++j) {
-                        if (tile == 0) ex[j] = 0;
-                        if (j < nvalid && lane == j) {
-                            const int b = bb + j;
-                            if (tile > 0) st_relaxed(slots + j * a.ntiles + tile, FP32 | (ex[j] + s_cnt[b]));
-                            s_gbase[b] = boff[b] + ex[j] - s_excl[b];
-                        }
-                    }
+                    s_gbase[b] = boff[b] + excl - s_excl[b];
                 }
             }
         }

@@ -17,7 +17,7 @@ namespace evosort {
 template <typename U, bool PAIRS, int BLOCK, int KPT, int D, int RANK>
 cudaError_t launch_onesweep_inst(size_t grid, int sms, cudaStream_t s, const RadixArgs& a, int pass) {
     auto kern = radix_onesweep<U, PAIRS, BLOCK, KPT, D, RANK>;
-    const size_t smem = onesweep_smem_bytes(BLOCK, KPT, (int)sizeof(U), PAIRS, D);
+    const size_t smem = onesweep_smem_bytes(BLOCK, KPT, (int)sizeof(U), PAIRS, D, RANK);
     static int resident = 0;   // resident CTAs per SM
     if (resident == 0) {
         cudaError_t e = cudaSuccess;
@@ -37,11 +37,22 @@ cudaError_t launch_onesweep_inst(size_t grid, int sms, cudaStream_t s, const Rad
     return cudaGetLastError();
 }
 
-// Digit widths 4..11 with per-bit ballot ranking; match.any ranking for d = 8.
+// Digit widths 4..11 with per-bit ballot ranking; shared match-mask ranking
+// for 4..8; match.any ranking for d = 8.
 template <typename U, bool PAIRS, int B, int K>
 cudaError_t launch_onesweep_d(int rank, size_t grid, int sms, cudaStream_t s, const RadixArgs& a, int pass) {
     if (rank == 1) {
         if (a.d == 8) return launch_onesweep_inst<U, PAIRS, B, K, 8, 1>(grid, sms, s, a, pass);
+        return cudaErrorInvalidConfiguration;
+    }
+    if (rank == 3) {
+        switch (a.d) {
+            case 4: return launch_onesweep_inst<U, PAIRS, B, K, 4, 3>(grid, sms, s, a, pass);
+            case 5: return launch_onesweep_inst<U, PAIRS, B, K, 5, 3>(grid, sms, s, a, pass);
+            case 6: return launch_onesweep_inst<U, PAIRS, B, K, 6, 3>(grid, sms, s, a, pass);
+            case 7: return launch_onesweep_inst<U, PAIRS, B, K, 7, 3>(grid, sms, s, a, pass);
+            case 8: return launch_onesweep_inst<U, PAIRS, B, K, 8, 3>(grid, sms, s, a, pass);
+        }
         return cudaErrorInvalidConfiguration;
     }
     switch (a.d) {
@@ -76,12 +87,16 @@ inline bool onesweep_shape_supported(int block, int kpt) {
 }
 
 // True if the tile shape is compiled in and its shared memory fits a CTA.
-inline bool onesweep_config_fits(int w, bool pairs, int block, int kpt, int d) {
-    return onesweep_shape_supported(block, kpt) && onesweep_smem_bytes(block, kpt, w, pairs, d) <= kMaxDynSmem;
+inline bool onesweep_config_fits(int w, bool pairs, int block, int kpt, int d, int rank) {
+    return onesweep_shape_supported(block, kpt) &&
+           onesweep_smem_bytes(block, kpt, w, pairs, d, rank) <= kMaxDynSmem;
 }
 
-// match.any ranking is compiled for 8-bit digits only.
-inline bool onesweep_rank_supported(int rank, int d) { return rank == 2 || (rank == 1 && d == 8); }
+// Compiled ranking variants: ballot for every width, shared match masks for
+// widths up to 8, match.any for 8-bit digits.
+inline bool onesweep_rank_supported(int rank, int d) {
+    return rank == 2 || (rank == 1 && d == 8) || (rank == 3 && d <= 8);
+}
 
 // Defined in radix32k.cu, radix32p.cu, radix64k.cu, radix64p.cu.
 cudaError_t launch_onesweep_u32_keys(int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,

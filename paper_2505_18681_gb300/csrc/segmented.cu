@@ -1,5 +1,5 @@
 // Batched segmented sort.
-#include "../../include/evosort.h"
+#include "evosort.h"
 #include "api_internal.h"
 
 extern "C" evosort_status evosort_segmented_sort(void* keys, const uint64_t* offsets, size_t nseg,

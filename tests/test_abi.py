@@ -81,7 +81,7 @@ def test_rejects_bad_arguments_without_a_gpu(lib):
 
 
 @pytest.mark.parametrize("field,value", [("digit_bits", 3), ("digit_bits", 12), ("algo", 7),
-                                         ("rank_mode", 3), ("insertion_threshold", 1),
+                                         ("rank_mode", 4), ("rank_mode", -1), ("insertion_threshold", 1),
                                          ("insertion_threshold", 4096), ("block_size", 100)])
 def test_rejects_bad_params(lib, field, value):
     p = _params(lib, **{field: value})

@@ -98,20 +98,23 @@ def test_digit_widths(evo, d, dtype):
     run_pairs(evo, x, inplace=True, algo="radix", digit_bits=d)
 
 
-def tile_fits(block, kpt, w, pairs, d):
+def tile_fits(block, kpt, w, pairs, d, rank):
     """Shared memory of one radix CTA: three tile buffers, per-warp digit
-    counters, digit offsets, counts and bases, two mbarriers (<= 227 KB less 1 KB)."""
-    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * (1 << d) * 2 + (1 << d) * 16 + 16
+    counters, digit offsets and bases, two mbarriers, per-warp match masks for
+    rank mode 3 (<= 227 KB less 1 KB)."""
+    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * (1 << d) * 2 + (1 << d) * 12 + 16
+    if rank == 3:
+        smem += block // 32 * (1 << d) * 4
     return smem <= 232448 - 1024
 
 
 @pytest.mark.parametrize("shape", [(256, 8), (256, 16), (256, 32), (512, 16), (512, 32)])
-@pytest.mark.parametrize("rank", [1, 2])
+@pytest.mark.parametrize("rank", [1, 2, 3])
 @pytest.mark.parametrize("d", [6, 8, 11])
 def test_tile_shapes_and_ranking(evo, shape, rank, d):
     """Every compiled tile shape and ranking variant; shapes whose tile does
-    not fit in shared memory, and match ranking at a width other than 8 bits,
-    must be rejected with ERR_INVALID."""
+    not fit in shared memory, match.any ranking at a width other than 8 bits
+    and match-mask ranking above 8 bits must be rejected with ERR_INVALID."""
     block, kpt = shape
     kw = dict(algo="radix", block_size=block, keys_per_thread=kpt, rank_mode=rank, digit_bits=d)
     for dtype in (torch.uint32, torch.int64):
@@ -119,7 +122,8 @@ def test_tile_shapes_and_ranking(evo, shape, rank, d):
         x = gen("zipf" if dtype == torch.int64 else "uniform", 150_011, dtype)
         for pairs in (False, True):
             runner = run_pairs if pairs else run_keys
-            if tile_fits(block, kpt, w, pairs, d) and (rank == 2 or d == 8):
+            compiled = rank == 2 or (rank == 1 and d == 8) or (rank == 3 and d <= 8)
+            if compiled and tile_fits(block, kpt, w, pairs, d, rank):
                 runner(evo, x, **kw)
             else:
                 with pytest.raises(evo.EvoSortError) as ei:
@@ -182,3 +186,12 @@ def test_repeated_calls_are_identical(evo):
         outs.append(y)
     evo.sync()
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
+
+
+@pytest.mark.parametrize("dist", ["sorted", "equal", "distinct16", "uniform1000"])
+def test_match_mask_ranking_low_entropy(evo, dist):
+    """Rank mode 3 when whole warps share a digit (its slow case) is still exact."""
+    for dtype in (torch.int32, torch.int64):
+        x = gen(dist, 200_003, dtype)
+        run_pairs(evo, x, algo="radix", rank_mode=3, digit_bits=8)
+        run_keys(evo, x, algo="radix", rank_mode=3, digit_bits=5)
