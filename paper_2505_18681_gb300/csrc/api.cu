@@ -262,7 +262,7 @@ using namespace evosort;
 static void defaults_for(int w, Plan* pl) {
     pl->algo = EVOSORT_ALGO_RADIX;
     pl->digit_bits = 8;
-    pl->block_size = 256;
+    pl->block_size = 1024;
     pl->keys_per_thread = w == 4 ? 16 : 8;
     pl->insertion_threshold = 32;
     pl->rank_mode = 3;
@@ -278,6 +278,7 @@ static int resolve(const evosort_params* p, int dt, Plan* pl, std::string* err) 
     if (p->keys_per_thread) pl->keys_per_thread = p->keys_per_thread;
     if (p->insertion_threshold) pl->insertion_threshold = p->insertion_threshold;
     if (p->rank_mode) pl->rank_mode = p->rank_mode;
+    else if (pl->digit_bits > 8) pl->rank_mode = 2;   // match masks are compiled for d <= 8
     if (pl->algo != EVOSORT_ALGO_RADIX && pl->algo != EVOSORT_ALGO_MERGE) {
         *err = "params.algo must be -1, 0 or 1";
         return EVOSORT_ERR_INVALID;
@@ -341,7 +342,8 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     int rc = resolve(p, dt, &pl, &err);
     if (rc) return finish(rc, err);
     if (pl.algo == EVOSORT_ALGO_RADIX &&
-        !onesweep_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits, pl.rank_mode))
+        (!onesweep_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits, pl.rank_mode) ||
+         !onesweep_rank_fits(pl.rank_mode, pl.block_size, pl.keys_per_thread, w, pl.digit_bits)))
         return finish(EVOSORT_ERR_INVALID, "radix tile does not fit in shared memory (block_size x "
                                            "keys_per_thread too large for this key width and digit width)");
     cudaStream_t s = p ? (cudaStream_t)p->stream : nullptr;

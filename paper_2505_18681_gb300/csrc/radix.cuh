@@ -231,11 +231,11 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t dig) {
 
 // Dynamic shared memory of one onesweep CTA: three tile buffers (two TMA
 // input buffers, one reorder buffer), per-warp digit counters, the tile's
-// digit offsets and global bases, two mbarriers, and for rank mode 3 the
-// per-warp match masks.
+// digit offsets and global bases, two mbarriers.  (Rank mode 3 keeps its
+// per-warp match masks in the reorder buffer.)
 __host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d, int rank) {
     return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * ((size_t)1 << d) * 2 +
-           ((size_t)1 << d) * 12 + 16 + (rank == 3 ? (size_t)(block / 32) * ((size_t)1 << d) * 4 : 0);
+           ((size_t)1 << d) * 12 + 16;
 }
 // Largest dynamic shared memory a CTA may use on sm_100-class GPUs (227 KB),
 // less room for the kernel's static shared variables.
@@ -315,7 +315,9 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     uint32_t* s_excl = (uint32_t*)(s_whist + WARPS * bins);
     unsigned long long* s_gbase = (unsigned long long*)(s_excl + bins);
     uint64_t* s_bar = (uint64_t*)(s_gbase + bins);
-    uint32_t* s_match = (uint32_t*)(s_bar + 2);   // RANK 3: WARPS x bins match masks
+    // RANK 3 match masks (WARPS x bins words) live in the reorder buffer,
+    // which is idle while a tile is ranked
+    uint32_t* s_match = (uint32_t*)s_rkeys;
     __shared__ uint32_t s_tile[2];
     __shared__ uint32_t s_scr[WARPS + 1];
 
@@ -327,8 +329,6 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     const bool use_tma = (((uintptr_t)src & 15) == 0) && (!PAIRS || (((uintptr_t)vsrc & 15) == 0));
     const size_t full_tiles = n / TILE;
 
-    if (RANK == 3)
-        for (int i = tid; i < WARPS * bins; i += BLOCK) s_match[i] = 0u;
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
@@ -371,6 +371,8 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         uint16_t* wh = s_whist + warp * bins;
         uint32_t* wm = s_match + warp * bins;
         for (int i = lane; i < bins / 2; i += 32) ((uint32_t*)wh)[i] = 0;
+        if (RANK == 3)
+            for (int i = lane; i < bins; i += 32) wm[i] = 0u;
 
         // ---- keys of the tile, warp-striped (warp w owns a contiguous run of
         // 32*KPT keys; key i of a lane sits at w*32*KPT + 32*i + lane).  The
@@ -469,7 +471,10 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                 ex += cnt[j];
             }
         }
-        // ---- decoupled look-back for the owned digits
+        __syncthreads();   // s_excl and the warp prefixes are complete
+        // ---- decoupled look-back for the owned digits.  No barrier follows:
+        // threads without digits to resolve go straight on to the reorder,
+        // which overlaps the look-back's L2 round trips.
         {
             const unsigned long long* boff = a.counts + (size_t)pass * bins;
 #pragma unroll
@@ -480,12 +485,12 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     const size_t slot0 = (size_t)pass * a.ntiles * bins + b;
                     if (tile > 0) {
                         if (a.lb64) {
-                            excl = lookback_digit<uint64_t, 8>((const uint64_t*)a.lookback + slot0, bins,
+                            excl = lookback_digit<uint64_t, 16>((const uint64_t*)a.lookback + slot0, bins,
                                                                tile, a.status);
                             st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
                                        FP64 | (excl + cnt[j]));
                         } else {
-                            excl = lookback_digit<uint32_t, 8>((const uint32_t*)a.lookback + slot0, bins,
+                            excl = lookback_digit<uint32_t, 16>((const uint32_t*)a.lookback + slot0, bins,
                                                                tile, a.status);
                             st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
                                        FP32 | (uint32_t)(excl + cnt[j]));
@@ -495,7 +500,6 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                 }
             }
         }
-        __syncthreads();
 
         // ---- reorder the tile by digit into the reorder buffer (stable)
         {
@@ -548,4 +552,11 @@ __global__ void __launch_bounds__(256) radix_fixup(RadixArgs a) {
     }
 }
 
+}  // namespace evosort
+
+namespace evosort {
+// The rank-3 match masks must fit in the reorder buffer.
+constexpr bool match_masks_fit(int block, int kpt, int w, int d) {
+    return (size_t)(block / 32) * ((size_t)1 << d) * 4 <= (size_t)block * kpt * w;
+}
 }  // namespace evosort

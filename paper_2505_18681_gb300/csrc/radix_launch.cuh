@@ -8,11 +8,11 @@ namespace evosort {
 
 // (threads per CTA, keys per thread) pairs compiled into the library.
 #define EVOSORT_TILE_SHAPES(X) \
-    X(256, 8)                  \
     X(256, 16)                 \
-    X(256, 32)                 \
     X(512, 16)                 \
-    X(512, 32)
+    X(512, 32)                 \
+    X(1024, 8)                 \
+    X(1024, 16)
 
 template <typename U, bool PAIRS, int BLOCK, int KPT, int D, int RANK>
 cudaError_t launch_onesweep_inst(size_t grid, int sms, cudaStream_t s, const RadixArgs& a, int pass) {
@@ -96,6 +96,9 @@ inline bool onesweep_config_fits(int w, bool pairs, int block, int kpt, int d, i
 // widths up to 8, match.any for 8-bit digits.
 inline bool onesweep_rank_supported(int rank, int d) {
     return rank == 2 || (rank == 1 && d == 8) || (rank == 3 && d <= 8);
+}
+inline bool onesweep_rank_fits(int rank, int block, int kpt, int w, int d) {
+    return rank != 3 || match_masks_fit(block, kpt, w, d);
 }
 
 // Defined in radix32k.cu, radix32p.cu, radix64k.cu, radix64p.cu.
