@@ -262,16 +262,40 @@ using namespace evosort;
 static void defaults_for(int w, Plan* pl) {
     pl->algo = EVOSORT_ALGO_RADIX;
     pl->digit_bits = 8;
-    pl->block_size = 1024;
-    pl->keys_per_thread = w == 4 ? 16 : 8;
+    pl->block_size = 0;        // chosen by default_tile_shape once pairs/d are known
+    pl->keys_per_thread = 0;
     pl->insertion_threshold = 32;
     pl->rank_mode = 3;
+    (void)w;
 }
 
-static int resolve(const evosort_params* p, int dt, Plan* pl, std::string* err) {
+// Default radix tile shape: the first of a preference list (largest tiles
+// first, so fewer tiles are in flight in the look-back) that fits.
+static void default_tile_shape(int w, bool pairs, Plan* pl) {
+    static const int pref4[][2] = {{512, 32}, {1024, 16}, {512, 16}, {1024, 8}, {256, 16}};
+    static const int pref8[][2] = {{1024, 8}, {512, 16}, {256, 16}, {1024, 16}, {512, 32}};
+    const int(*pref)[2] = w == 4 ? pref4 : pref8;
+    for (int i = 0; i < 5; ++i) {
+        const int b = pl->block_size ? pl->block_size : pref[i][0];
+        const int k = pl->keys_per_thread ? pl->keys_per_thread : pref[i][1];
+        if (onesweep_config_fits(w, pairs, b, k, pl->digit_bits, pl->rank_mode) &&
+            onesweep_rank_fits(pl->rank_mode, b, k, w, pl->digit_bits)) {
+            pl->block_size = b;
+            pl->keys_per_thread = k;
+            return;
+        }
+    }
+    if (!pl->block_size) pl->block_size = 256;
+    if (!pl->keys_per_thread) pl->keys_per_thread = 16;
+}
+
+static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::string* err) {
     const int w = dtype_bytes(dt);
     defaults_for(w, pl);
-    if (!p) return EVOSORT_OK;
+    if (!p) {
+        default_tile_shape(w, pairs, pl);
+        return EVOSORT_OK;
+    }
     if (p->algo != EVOSORT_ALGO_AUTO) pl->algo = p->algo;
     if (p->digit_bits) pl->digit_bits = p->digit_bits;
     if (p->block_size) pl->block_size = p->block_size;
@@ -299,6 +323,8 @@ static int resolve(const evosort_params* p, int dt, Plan* pl, std::string* err) 
         *err = "params.rank_mode: 1 (match.any) needs digit_bits 8, 3 (match masks) needs digit_bits <= 8";
         return EVOSORT_ERR_INVALID;
     }
+    if (pl->algo == EVOSORT_ALGO_RADIX && (!pl->block_size || !pl->keys_per_thread))
+        default_tile_shape(dtype_bytes(dt), pairs, pl);
     if (pl->algo == EVOSORT_ALGO_RADIX && !onesweep_shape_supported(pl->block_size, pl->keys_per_thread)) {
         *err = "params.block_size/keys_per_thread: unsupported radix tile shape";
         return EVOSORT_ERR_INVALID;
@@ -339,7 +365,7 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     if (n >= (1ull << 40)) return finish(EVOSORT_ERR_UNSUPPORTED, "n >= 2^40");
     if (pairs && n > 0xFFFFFFFFull) return finish(EVOSORT_ERR_UNSUPPORTED, "key/value sorts need n < 2^32");
     Plan pl;
-    int rc = resolve(p, dt, &pl, &err);
+    int rc = resolve(p, dt, pairs, &pl, &err);
     if (rc) return finish(rc, err);
     if (pl.algo == EVOSORT_ALGO_RADIX &&
         (!onesweep_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits, pl.rank_mode) ||
@@ -390,7 +416,7 @@ size_t evosort_workspace_bytes(size_t n, evosort_dtype dt, int with_values, cons
     std::string err;
     if (!valid_dtype(dt)) return 0;
     Plan pl;
-    if (resolve(p, dt, &pl, &err)) return 0;
+    if (resolve(p, dt, with_values != 0, &pl, &err)) return 0;
     const int w = dtype_bytes(dt);
     if (pl.algo == EVOSORT_ALGO_MERGE) return merge_workspace_bytes(n, w, with_values != 0, pl);
     return radix_workspace_bytes(n, w, with_values != 0, pl);
