@@ -314,6 +314,17 @@ def main():
     total_alg = sum(r["bytes"] for r in recs)
     shares = {k: round(v["ms"] / max(sum(x["ms"] for x in by_kind.values()), 1e-9), 4) for k, v in by_kind.items()}
 
+    # per-distribution device time of one sort each (diagnostic, after the timed region)
+    per_dist = {}
+    for d, x, p in zip(dists, xs, params):
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        evo.sort(x, out=out, params=p)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        per_dist[d] = round(f0.elapsed_time(f1), 3)
+
     # end to end: pinned host input -> device, sort, device -> pinned host output
     e2e = None
     if not args.no_e2e and rank == 0 or (not args.no_e2e and ws > 1):
@@ -344,6 +355,7 @@ def main():
                          "avg_active_launch_ms": (sum(r["ms"] for r in act) / len(act)) if act else None},
             "whole_step_alg_gbs": total_alg / args.steps / 1e9 / (ms_step * 1e-3),
             "kernel_time_share": shares,
+            "per_dist_ms": per_dist,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": launches,

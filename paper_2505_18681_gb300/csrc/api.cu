@@ -217,7 +217,7 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     const int sms = sm_count();
     const size_t hist_smem = (size_t)L.npass * ((size_t)1 << pl.digit_bits) * sizeof(uint32_t);
     size_t hist_grid = (n + 512 * 16 - 1) / (512 * 16);
-    if (hist_grid > (size_t)sms * 2) hist_grid = (size_t)sms * 2;
+    if (hist_grid > (size_t)sms * 4) hist_grid = (size_t)sms * 4;
     if (hist_grid < 1) hist_grid = 1;
     const int vb = pairs ? 4 : 0;
     const double pass_bytes = 2.0 * (double)n * (w + vb);

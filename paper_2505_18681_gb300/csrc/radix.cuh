@@ -75,64 +75,88 @@ __device__ __forceinline__ uint32_t* sel_vdst(const RadixArgs& a, int s) {
 
 // ---------------------------------------------------------------------------
 // K1: digit histograms of every pass in one read of the keys.
-// Shared counters per CTA (npass << d of them); consecutive equal digits of a
-// thread's keys are merged before the shared atomic, which keeps sorted and
-// low-entropy inputs from serialising on one counter.
+// Shared counters per CTA (npass << d of them).  Each thread reads a run of
+// HC consecutive keys and merges consecutive equal digits before the shared
+// atomic; when a whole warp ends its runs on the same digit (sorted and
+// low-entropy inputs) the warp adds one reduced count instead of 32.
 // ---------------------------------------------------------------------------
+template <typename U>
+__device__ __forceinline__ void hist_add_run(uint32_t* h, uint32_t dig, uint32_t run, bool warp_full) {
+    if (warp_full) {
+        const uint32_t d0 = __shfl_sync(0xffffffffu, dig, 0);
+        if (__all_sync(0xffffffffu, dig == d0)) {
+            const uint32_t t = __reduce_add_sync(0xffffffffu, run);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&h[d0], t);
+            return;
+        }
+    }
+    atomicAdd(&h[dig], run);
+}
+
 template <typename U>
 __global__ void __launch_bounds__(512) radix_histogram(RadixArgs a) {
     extern __shared__ uint32_t s_h[];
     const int bins = 1 << a.d;
     const int total = a.npass * bins;
-    const U mask = (U)(bins - 1);
+    const uint32_t mask = (uint32_t)(bins - 1);
     for (int i = threadIdx.x; i < total; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
 
     constexpr int V = 16 / sizeof(U);   // keys per 128-bit load
+    constexpr int HC = 16;              // keys per thread run
     const U* keys = (const U*)a.in;
     const size_t n = a.n;
-    // 16-byte aligned body; the head and tail are read with scalar loads
+    const KeyMap map = a.map;
+    // 16-byte aligned body of whole runs; the head and tail use scalar loads
     size_t head = ((16 - ((uintptr_t)keys & 15)) & 15) / sizeof(U);
     if (head > n) head = n;
-    const size_t nvec = (n - head) / V;
-    const size_t tail0 = head + nvec * V;
+    const size_t nruns = (n - head) / HC;
+    const size_t tail0 = head + nruns * HC;
     const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t gthreads = (size_t)gridDim.x * blockDim.x;
 
     auto count_key = [&](U k) {
-        k = map_fwd(k, a.map);
-        for (int p = 0; p < a.npass; ++p) {
-            const uint32_t dig = (uint32_t)((k >> (p * a.d)) & mask);
-            atomicAdd(&s_h[p * bins + dig], 1u);
-        }
+        k = map_fwd(k, map);
+        for (int p = 0; p < a.npass; ++p) atomicAdd(&s_h[p * bins + digit_of(k, p * a.d, mask)], 1u);
     };
     if (gtid < head) count_key(keys[gtid]);
     if (gtid < n - tail0) count_key(keys[tail0 + gtid]);
 
-    using Vec = uint4;
-    const Vec* vp = (const Vec*)(keys + head);
-    for (size_t i = gtid; i < nvec; i += gthreads) {
-        Vec v = __ldcs(vp + i);
-        U k[V];
-        memcpy(k, &v, 16);
+    // warps take 32 consecutive runs at a time, one run per lane
+    const size_t warp_id = gtid >> 5;
+    const size_t nwarps = gthreads >> 5;
+    const int lane = threadIdx.x & 31;
+    for (size_t r0 = warp_id * 32; r0 < nruns; r0 += nwarps * 32) {
+        const size_t r = r0 + lane;
+        const bool warp_full = r0 + 32 <= nruns;
+        if (r < nruns) {
+            U k[HC];
+            const uint4* vp = (const uint4*)(keys + head + r * HC);
 #pragma unroll
-        for (int j = 0; j < V; ++j) k[j] = map_fwd(k[j], a.map);
-        for (int p = 0; p < a.npass; ++p) {
-            const int sh = p * a.d;
-            uint32_t prev = (uint32_t)((k[0] >> sh) & mask);
-            uint32_t run = 1;
-#pragma unroll
-            for (int j = 1; j < V; ++j) {
-                const uint32_t dig = (uint32_t)((k[j] >> sh) & mask);
-                if (dig == prev) {
-                    ++run;
-                } else {
-                    atomicAdd(&s_h[p * bins + prev], run);
-                    prev = dig;
-                    run = 1;
-                }
+            for (int j = 0; j < HC / V; ++j) {
+                const uint4 v = vp[j];
+                memcpy(&k[j * V], &v, 16);
             }
-            atomicAdd(&s_h[p * bins + prev], run);
+#pragma unroll
+            for (int j = 0; j < HC; ++j) k[j] = map_fwd(k[j], map);
+            for (int p = 0; p < a.npass; ++p) {
+                const int sh = p * a.d;
+                uint32_t* h = s_h + p * bins;
+                uint32_t cur = digit_of(k[0], sh, mask);
+                uint32_t run = 1;
+#pragma unroll
+                for (int j = 1; j < HC; ++j) {
+                    const uint32_t dg = digit_of(k[j], sh, mask);
+                    if (dg == cur) {
+                        ++run;
+                    } else {
+                        atomicAdd(&h[cur], run);
+                        cur = dg;
+                        run = 1;
+                    }
+                }
+                hist_add_run<U>(h, cur, run, warp_full);
+            }
         }
     }
     __syncthreads();
@@ -209,9 +233,9 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
 //
 // Persistent CTAs take tiles in order from an atomic counter, so every tile's
 // predecessors are held by running CTAs and the look-back always progresses.
-// A CTA claims its next tile while it works on the current one and has the
-// TMA engine copy that tile (keys, and values for pairs) into the other half
-// of a double input buffer; a third buffer receives the reordered tile.
+// A CTA claims its next tile once the current one's aggregates are published
+// and has the TMA engine copy it (keys, and values for pairs) into the other
+// half of a double input buffer; a third buffer receives the reordered tile.
 // ---------------------------------------------------------------------------
 template <int RANK, int D>
 __device__ __forceinline__ uint32_t warp_peers(uint32_t dig) {
@@ -353,18 +377,6 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         if (tile >= a.ntiles) break;
         const size_t base = (size_t)tile * TILE;
         const bool full = tile < full_tiles;
-        // claim the next tile and start copying it into the other buffer
-        if (tid == 0) {
-            const uint32_t nx = atomicAdd(a.tile_counter + pass, 1u);
-            s_tile[cur ^ 1] = nx;
-            if (use_tma && nx < full_tiles) {
-                unsigned char* nb = bufs + (cur ^ 1) * (KB + VB);
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&s_bar[cur ^ 1], (uint32_t)(KB + VB));
-                bulk_load(nb, src + (size_t)nx * TILE, (uint32_t)KB, &s_bar[cur ^ 1]);
-                if (PAIRS) bulk_load(nb + KB, vsrc + (size_t)nx * TILE, (uint32_t)VB, &s_bar[cur ^ 1]);
-            }
-        }
         unsigned char* kb = bufs + cur * (KB + VB);
         U* s_keys = (U*)kb;
         uint32_t* s_vals = (uint32_t*)(kb + KB);
@@ -459,6 +471,21 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | s);
                 else
                     st_relaxed((uint32_t*)a.lookback + slot, (tile == 0 ? FP32 : FA32) | s);
+            }
+        }
+        // Claim the next tile only now, once this tile's aggregates are out:
+        // a claimed tile blocks the look-back of every later tile until its
+        // holder ranks it, so claims are made as late as the prefetch allows.
+        // The TMA engine copies it into the other input buffer meanwhile.
+        if (tid == 0) {
+            const uint32_t nx = atomicAdd(a.tile_counter + pass, 1u);
+            s_tile[cur ^ 1] = nx;
+            if (use_tma && nx < full_tiles) {
+                unsigned char* nb = bufs + (cur ^ 1) * (KB + VB);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&s_bar[cur ^ 1], (uint32_t)(KB + VB));
+                bulk_load(nb, src + (size_t)nx * TILE, (uint32_t)KB, &s_bar[cur ^ 1]);
+                if (PAIRS) bulk_load(nb + KB, vsrc + (size_t)nx * TILE, (uint32_t)VB, &s_bar[cur ^ 1]);
             }
         }
         {
