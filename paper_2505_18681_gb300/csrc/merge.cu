@@ -1,18 +1,333 @@
-// Bottom-up mergesort (Algorithm 3 of the paper).
+// Bottom-up parallel mergesort (Algorithm 3 of the paper, RefinedParallelMergeSort):
+// the array is cut into base runs of chunkSize = T_insertion keys, each run is
+// insertion-sorted, then runs are merged pairwise with the run length
+// doubling (currSize, 2 currSize, ...) until one run remains.  A run without
+// a partner is carried to the next round unchanged.
+//
+// GPU mapping:
+//   K4 merge_block_sort   one CTA per tile of T = T_ins * 2^m keys (the largest
+//                         such tile that fits): loads the tile into shared
+//                         memory, insertion-sorts its base runs (one thread per
+//                         run), then performs the in-tile merge rounds in shared
+//                         memory with merge-path splits per thread;
+//   K5 merge_partition    for each global round, the merge-path split of every
+//                         output tile boundary (binary search along the
+//                         cross-diagonal of the two runs of its pair);
+//   K6 merge_pass         one CTA per output tile: stages its slices of the two
+//                         runs in shared memory, merges them (merge-path per
+//                         thread) and writes the tile coalesced.
+// All merges are stable: on equal keys the left run's key comes first.  Keys
+// are compared through the order-preserving map of their dtype, applied on the
+// first load and undone on the last store.
 #include "evosort.h"
 #include "api_internal.h"
 #include "common.cuh"
 
 namespace evosort {
 
-size_t merge_workspace_bytes(size_t n, int w, bool pairs, const Plan&) {
-    return ((n * w + 255) / 256 + (pairs ? (n * 4 + 255) / 256 : 0)) * 256 + 256;
+namespace {
+
+constexpr int kMB = 256;       // threads per CTA
+constexpr int kMEPT = 16;      // keys per thread
+constexpr int kMTile = kMB * kMEPT;   // keys per CTA tile (global merge rounds)
+
+struct MergeArgs {
+    const void* in;
+    void* out;
+    void* tmp;
+    const uint32_t* vin;
+    uint32_t* vout;
+    uint32_t* vtmp;
+    size_t n;
+    KeyMap map;
+    int tins;        // base run length (insertion threshold)
+    int btile;       // block-sort tile: tins * 2^m <= kMTile
+};
+
+// Merge-path split: number of keys of run A among the first k outputs of the
+// stable merge of A (length la) and B (length lb).
+template <typename U, typename AccA, typename AccB>
+__device__ __forceinline__ size_t merge_path(AccA A, size_t la, AccB B, size_t lb, size_t k) {
+    size_t lo = k > lb ? k - lb : 0;
+    size_t hi = k < la ? k : la;
+    while (lo < hi) {
+        const size_t mid = (lo + hi) >> 1;
+        if ((U)B(k - 1 - mid) < (U)A(mid))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
 }
 
-int merge_sort(const void*, void*, const uint32_t*, uint32_t*, size_t, int, const Plan&, void*, size_t,
-               cudaStream_t, std::string* err) {
-    *err = "mergesort not built yet";
-    return EVOSORT_ERR_UNSUPPORTED;
+// ---------------------------------------------------------------------------
+// K4: block sort of one tile (base runs insertion-sorted, then merged).
+// ---------------------------------------------------------------------------
+template <typename U, bool PAIRS>
+__global__ void __launch_bounds__(kMB) merge_block_sort(MergeArgs a, int dst_sel, int last) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    U* k0 = (U*)smem;
+    U* k1 = k0 + kMTile;
+    uint32_t* v0 = (uint32_t*)(k1 + kMTile);
+    uint32_t* v1 = v0 + (PAIRS ? kMTile : 0);
+    const int T = a.btile;
+    const size_t base = (size_t)blockIdx.x * T;
+    const int len = (int)((a.n - base) < (size_t)T ? (a.n - base) : (size_t)T);
+    const U* src = (const U*)a.in;
+    for (int i = threadIdx.x; i < len; i += kMB) {
+        k0[i] = map_fwd(src[base + i], a.map);
+        if (PAIRS) v0[i] = a.vin[base + i];
+    }
+    __syncthreads();
+    // insertion sort of each base run (Algorithm 3, InsertionSort on chunks)
+    const int runs = (len + a.tins - 1) / a.tins;
+    for (int r = threadIdx.x; r < runs; r += kMB) {
+        const int lo = r * a.tins;
+        const int hi = lo + a.tins < len ? lo + a.tins : len;
+        for (int i = lo + 1; i < hi; ++i) {
+            const U key = k0[i];
+            uint32_t val = PAIRS ? v0[i] : 0u;
+            int j = i;
+            while (j > lo && k0[j - 1] > key) {   // strictly greater: stable
+                k0[j] = k0[j - 1];
+                if (PAIRS) v0[j] = v0[j - 1];
+                --j;
+            }
+            k0[j] = key;
+            if (PAIRS) v0[j] = val;
+        }
+    }
+    __syncthreads();
+    // merge rounds inside the tile (MergeStandardOpt, currSize doubling)
+    const int chunk = (len + kMB - 1) / kMB;
+    U* ks = k0;
+    U* kd = k1;
+    uint32_t* vs = v0;
+    uint32_t* vd = v1;
+    for (int w = a.tins; w < len; w <<= 1) {
+        int o = threadIdx.x * chunk;
+        const int oend = o + chunk < len ? o + chunk : len;
+        while (o < oend) {
+            const int pbase = (o / (2 * w)) * (2 * w);
+            const int la = (pbase + w < len ? pbase + w : len) - pbase;
+            const int lb = (pbase + 2 * w < len ? pbase + 2 * w : len) - pbase - la;
+            const U* A = ks + pbase;
+            const U* B = A + la;
+            const int k = o - pbase;
+            int ia = (int)merge_path<U>([&](size_t i) { return A[i]; }, la, [&](size_t i) { return B[i]; }, lb,
+                                        (size_t)k);
+            int ib = k - ia;
+            const int stop = (pbase + la + lb < oend ? pbase + la + lb : oend);
+            for (; o < stop; ++o) {
+                const bool takeB = ia >= la || (ib < lb && B[ib] < A[ia]);
+                if (takeB) {
+                    kd[o] = B[ib];
+                    if (PAIRS) vd[o] = vs[pbase + la + ib];
+                    ++ib;
+                } else {
+                    kd[o] = A[ia];
+                    if (PAIRS) vd[o] = vs[pbase + ia];
+                    ++ia;
+                }
+            }
+        }
+        __syncthreads();
+        U* t = ks; ks = kd; kd = t;
+        uint32_t* tv = vs; vs = vd; vd = tv;
+    }
+    U* dst = dst_sel ? (U*)a.tmp : (U*)a.out;
+    uint32_t* vdst = dst_sel ? a.vtmp : a.vout;
+    for (int i = threadIdx.x; i < len; i += kMB) {
+        dst[base + i] = last ? map_inv(ks[i], a.map) : ks[i];
+        if (PAIRS) vdst[base + i] = vs[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: merge-path splits of every output tile boundary for runs of width w.
+// split[j] = keys of the left run of its pair among outputs [pair start, j*T).
+// ---------------------------------------------------------------------------
+template <typename U>
+__global__ void __launch_bounds__(256) merge_partition(const U* __restrict__ src, size_t n, size_t w,
+                                                       size_t ntiles, size_t* __restrict__ split) {
+    const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > ntiles) return;
+    size_t o = j * kMTile;
+    if (o > n) o = n;
+    const size_t pbase = (o / (2 * w)) * (2 * w);
+    const size_t la = (pbase + w < n ? pbase + w : n) - pbase;
+    const size_t lb = (pbase + 2 * w < n ? pbase + 2 * w : n) - pbase - la;
+    const U* A = src + pbase;
+    const U* B = A + la;
+    split[j] = merge_path<U>([&](size_t i) { return A[i]; }, la, [&](size_t i) { return B[i]; }, lb, o - pbase);
+}
+
+// ---------------------------------------------------------------------------
+// K6: one output tile of a global merge round.
+// ---------------------------------------------------------------------------
+template <typename U, bool PAIRS>
+__global__ void __launch_bounds__(kMB) merge_pass(const U* __restrict__ src, U* __restrict__ dst,
+                                                  const uint32_t* __restrict__ vsrc, uint32_t* __restrict__ vdst,
+                                                  size_t n, size_t w, const size_t* __restrict__ split, KeyMap map,
+                                                  int last) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    U* sk = (U*)smem;                          // staged slices
+    U* so = sk + kMTile;                       // merged output
+    uint32_t* sv = (uint32_t*)(so + kMTile);
+    uint32_t* sov = sv + (PAIRS ? kMTile : 0);
+    const size_t j = blockIdx.x;
+    const size_t o0 = j * kMTile;
+    const size_t o1 = o0 + kMTile < n ? o0 + kMTile : n;
+    // the tile may straddle one pair boundary; handle each piece in turn
+    size_t o = o0;
+    int piece = 0;
+    while (o < o1) {
+        const size_t pbase = (o / (2 * w)) * (2 * w);
+        const size_t la = (pbase + w < n ? pbase + w : n) - pbase;
+        const size_t lb = (pbase + 2 * w < n ? pbase + 2 * w : n) - pbase - la;
+        const size_t pend = pbase + la + lb;
+        const size_t e = pend < o1 ? pend : o1;
+        // splits at o and e within this pair
+        const size_t ka = o - pbase, kb = e - pbase;
+        // a piece that starts the tile starts at split[j]; a second piece starts
+        // at its pair's beginning.  A piece ends at the pair's end, or at the
+        // tile end, whose split (relative to the same pair) is split[j + 1].
+        const size_t a0 = (piece == 0) ? split[j] : 0;
+        const size_t a1 = (e == pend) ? la : split[j + 1];
+        const size_t b0 = ka - a0, b1 = kb - a1;
+        const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
+        const U* A = src + pbase + a0;
+        const U* B = src + pbase + la + b0;
+        for (int i = threadIdx.x; i < na + nb; i += kMB) {
+            const bool inA = i < na;
+            sk[i] = inA ? A[i] : B[i - na];
+            if (PAIRS) sv[i] = inA ? vsrc[pbase + a0 + i] : vsrc[pbase + la + b0 + (i - na)];
+        }
+        __syncthreads();
+        const int cnt = na + nb;
+        const int chunk = (cnt + kMB - 1) / kMB;
+        const int q0 = threadIdx.x * chunk < cnt ? threadIdx.x * chunk : cnt;
+        const int q1 = q0 + chunk < cnt ? q0 + chunk : cnt;
+        if (q0 < q1) {
+            const U* SA = sk;
+            const U* SB = sk + na;
+            int ia = (int)merge_path<U>([&](size_t i) { return SA[i]; }, na, [&](size_t i) { return SB[i]; }, nb,
+                                        (size_t)q0);
+            int ib = q0 - ia;
+            for (int q = q0; q < q1; ++q) {
+                const bool takeB = ia >= na || (ib < nb && SB[ib] < SA[ia]);
+                if (takeB) {
+                    so[q] = SB[ib];
+                    if (PAIRS) sov[q] = sv[na + ib];
+                    ++ib;
+                } else {
+                    so[q] = SA[ia];
+                    if (PAIRS) sov[q] = sv[ia];
+                    ++ia;
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += kMB) {
+            dst[o + i] = last ? map_inv(so[i], map) : so[i];
+            if (PAIRS) vdst[o + i] = sov[i];
+        }
+        __syncthreads();
+        o = e;
+        ++piece;
+    }
+}
+
+template <typename U, bool PAIRS>
+int merge_sort_t(const MergeArgs& a0, void* ws, cudaStream_t s, std::string* err) {
+    MergeArgs a = a0;
+    const size_t n = a.n;
+    // global rounds after the block sort
+    int rounds = 0;
+    for (size_t w = (size_t)a.btile; w < n; w <<= 1) ++rounds;
+    const size_t ntiles = (n + kMTile - 1) / kMTile;
+    size_t* split = (size_t*)ws;
+    const size_t smem_block = (size_t)2 * kMTile * (sizeof(U) + (PAIRS ? 4 : 0));
+    const size_t smem_pass = smem_block;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(merge_block_sort<U, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_block);
+        cudaFuncSetAttribute(merge_pass<U, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pass);
+        configured = true;
+    }
+    // block sort: destination chosen so the last round ends in out
+    const int dst_sel = (rounds % 2 == 1) ? 1 : 0;   // 1 = tmp
+    const size_t nblk = (n + a.btile - 1) / a.btile;
+    const int call = prof_call_begin(nullptr, 0, s);
+    {
+        ProfScope ps(call, EVOSORT_K_MERGE_BLOCK, -1, 2.0 * n * (sizeof(U) + (PAIRS ? 4 : 0)), n, s);
+        merge_block_sort<U, PAIRS><<<(unsigned)nblk, kMB, smem_block, s>>>(a, dst_sel, rounds == 0);
+    }
+    count_launches(1);
+    const U* src = dst_sel ? (const U*)a.tmp : (const U*)a.out;
+    U* dst = dst_sel ? (U*)a.out : (U*)a.tmp;
+    const uint32_t* vsrc = dst_sel ? a.vtmp : a.vout;
+    uint32_t* vdst = dst_sel ? a.vout : a.vtmp;
+    int r = 0;
+    for (size_t w = (size_t)a.btile; w < n; w <<= 1, ++r) {
+        {
+            ProfScope ps(call, EVOSORT_K_MERGE_PARTITION, r, 0.0, ntiles + 1, s);
+            merge_partition<U><<<(unsigned)((ntiles + 1 + 255) / 256), 256, 0, s>>>(src, n, w, ntiles, split);
+        }
+        {
+            ProfScope ps(call, EVOSORT_K_MERGE_PASS, r, 2.0 * n * (sizeof(U) + (PAIRS ? 4 : 0)), n, s);
+            merge_pass<U, PAIRS><<<(unsigned)ntiles, kMB, smem_pass, s>>>(src, dst, vsrc, vdst, n, w, split, a.map,
+                                                                          r == rounds - 1);
+        }
+        count_launches(2);
+        const U* t = src; src = dst; dst = (U*)t;
+        const uint32_t* tv = vsrc; vsrc = vdst; vdst = (uint32_t*)tv;
+    }
+    prof_call_end(call, s, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("merge launch: ") + cudaGetErrorString(e);
+        return EVOSORT_ERR_CUDA;
+    }
+    return EVOSORT_OK;
+}
+
+}  // namespace
+
+static size_t merge_split_bytes(size_t n) {
+    return (((n + kMTile - 1) / kMTile + 2) * sizeof(size_t) + 255) / 256 * 256;
+}
+
+size_t merge_workspace_bytes(size_t n, int w, bool pairs, const Plan&) {
+    return merge_split_bytes(n) + (n * w + 255) / 256 * 256 + (pairs ? (n * 4 + 255) / 256 * 256 : 0);
+}
+
+int merge_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt, const Plan& pl,
+               void* ws, size_t ws_bytes, cudaStream_t s, std::string* err) {
+    const int w = dtype_bytes(dt);
+    const bool pairs = vout != nullptr;
+    if (ws_bytes < merge_workspace_bytes(n, w, pairs, pl)) {
+        *err = "workspace too small";
+        return EVOSORT_ERR_NOMEM;
+    }
+    MergeArgs a;
+    a.in = in;
+    a.out = out;
+    char* base = (char*)ws + merge_split_bytes(n);
+    a.tmp = base;
+    a.vin = vin;
+    a.vout = vout;
+    a.vtmp = pairs ? (uint32_t*)(base + (n * w + 255) / 256 * 256) : nullptr;
+    a.n = n;
+    a.map = key_map_for(dt);
+    a.tins = pl.insertion_threshold;
+    int t = a.tins;
+    while (t * 2 <= kMTile) t *= 2;
+    a.btile = t;
+    if (w == 4)
+        return pairs ? merge_sort_t<uint32_t, true>(a, ws, s, err) : merge_sort_t<uint32_t, false>(a, ws, s, err);
+    return pairs ? merge_sort_t<uint64_t, true>(a, ws, s, err) : merge_sort_t<uint64_t, false>(a, ws, s, err);
 }
 
 }  // namespace evosort
