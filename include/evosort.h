@@ -87,6 +87,10 @@ typedef struct {
                                  equal digits): 1 = match.any (d = 8 only),
                                  2 = one ballot per digit bit (any d),
                                  3 = shared-memory match masks (d <= 8; default) */
+    int seg_block_cap;        /* segmented sort: segments up to this many keys are
+                                 sorted by one CTA in shared memory, longer ones by
+                                 a CTA-local radix sort; 256..8192 (32-bit keys),
+                                 256..4096 (64-bit keys); default the maximum */
     void* stream;             /* cudaStream_t */
     void* workspace;          /* optional caller scratch, device, 256-B aligned */
     size_t workspace_bytes;
@@ -121,13 +125,26 @@ evosort_status evosort_sort_pairs_to(const void* keys_in, const uint32_t* values
                                      uint32_t* values_out, size_t n, evosort_dtype dt,
                                      const evosort_params* p);
 
-/* Sorts each segment keys[offsets[i] .. offsets[i+1]) independently, in place,
- * for i in [0, nseg).  offsets: DEVICE array of nseg + 1 uint64, non-decreasing,
- * offsets[0] == 0 (empty segments allowed).  Keys never cross a segment
- * boundary.  The offsets are validated on the device; a violation is reported
- * by evosort_sync() as EVOSORT_ERR_INVALID and the keys are left unsorted. */
-evosort_status evosort_segmented_sort(void* keys, const uint64_t* offsets, size_t nseg,
+/* Batched segmented sort: sorts each segment keys[offsets[i] .. offsets[i+1])
+ * independently, in place, for i in [0, nseg), in one persistent launch
+ * (after three small list-building kernels).  Short segments are sorted by
+ * one warp in registers, medium ones by one CTA in shared memory, long ones
+ * by a CTA-local LSD radix sort (Algorithms 4a/4b) over global memory.
+ *   keys    DEVICE array of total keys of dtype dt
+ *   total   number of keys, which must equal offsets[nseg]
+ *   offsets DEVICE array of nseg + 1 uint64: offsets[0] == 0, non-decreasing,
+ *           offsets[nseg] == total; empty segments are allowed.
+ * Keys never cross a segment boundary.  Equal keys are identical bit patterns,
+ * so the result is unique although the warp tier is not a stable network.
+ * The offsets are checked on the device; a violation is reported by the next
+ * evosort_sync() as EVOSORT_ERR_INVALID (keys in segments that were processed
+ * may then have been sorted).  Segments longer than 2^32 keys are not
+ * supported. */
+evosort_status evosort_segmented_sort(void* keys, size_t total, const uint64_t* offsets, size_t nseg,
                                       evosort_dtype dt, const evosort_params* p);
+
+/* Scratch bytes evosort_segmented_sort needs for total keys in nseg segments. */
+size_t evosort_segmented_workspace_bytes(size_t total, size_t nseg, evosort_dtype dt);
 
 /* Waits for params-stream work (stream = NULL: the legacy default stream) and
  * returns the first error recorded on the device since the last call

@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
     """Mirror of ``evosort_params``."""
     _fields_ = [("algo", ctypes.c_int), ("digit_bits", ctypes.c_int), ("keys_per_thread", ctypes.c_int),
                 ("block_size", ctypes.c_int), ("insertion_threshold", ctypes.c_int),
-                ("rank_mode", ctypes.c_int), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("rank_mode", ctypes.c_int), ("seg_block_cap", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
 
@@ -80,9 +81,10 @@ def library():
             lib.evosort_sort_pairs_to.argtypes = [vp, vp, vp, vp, sz, i, pp]
             for f in (lib.evosort_sort, lib.evosort_sort_to, lib.evosort_sort_pairs, lib.evosort_sort_pairs_to):
                 f.restype = st
-            if hasattr(lib, "evosort_segmented_sort"):
-                lib.evosort_segmented_sort.argtypes = [vp, vp, sz, i, pp]
-                lib.evosort_segmented_sort.restype = st
+            lib.evosort_segmented_sort.argtypes = [vp, sz, vp, sz, i, pp]
+            lib.evosort_segmented_sort.restype = st
+            lib.evosort_segmented_workspace_bytes.argtypes = [sz, sz, i]
+            lib.evosort_segmented_workspace_bytes.restype = sz
             lib.evosort_sync.argtypes = [vp]
             lib.evosort_sync.restype = st
             lib.evosort_last_error.argtypes = []
@@ -129,7 +131,7 @@ def _stream_handle(stream) -> int:
 
 
 def make_params(algo=None, digit_bits=0, keys_per_thread=0, block_size=0, insertion_threshold=0,
-                rank_mode=0, stream=None, workspace: torch.Tensor | None = None) -> Params:
+                rank_mode=0, seg_block_cap=0, stream=None, workspace: torch.Tensor | None = None) -> Params:
     p = Params()
     library().evosort_default_params(ctypes.byref(p))
     p.algo = ALGOS[algo]
@@ -138,6 +140,7 @@ def make_params(algo=None, digit_bits=0, keys_per_thread=0, block_size=0, insert
     p.block_size = int(block_size or 0)
     p.insertion_threshold = int(insertion_threshold or 0)
     p.rank_mode = int(rank_mode or 0)
+    p.seg_block_cap = int(seg_block_cap or 0)
     p.stream = _stream_handle(stream)
     if workspace is not None:
         p.workspace = workspace.data_ptr()
@@ -189,8 +192,8 @@ def segmented_sort(keys: torch.Tensor, offsets: torch.Tensor, *, params: Params 
     if offsets.dtype not in (torch.int64, torch.uint64):
         raise ValueError("offsets must be int64 or uint64")
     p = params if params is not None else make_params(**kw)
-    _check(library().evosort_segmented_sort(keys.data_ptr(), offsets.data_ptr(), offsets.numel() - 1,
-                                            _dtype_code(keys), ctypes.byref(p)))
+    _check(library().evosort_segmented_sort(keys.data_ptr(), keys.numel(), offsets.data_ptr(),
+                                            offsets.numel() - 1, _dtype_code(keys), ctypes.byref(p)))
     return keys
 
 

@@ -266,7 +266,7 @@ static void defaults_for(int w, Plan* pl) {
     pl->keys_per_thread = 0;
     pl->insertion_threshold = 32;
     pl->rank_mode = 3;
-    (void)w;
+    pl->seg_block_cap = w == 4 ? 8192 : 4096;
 }
 
 // Default radix tile shape: the first of a preference list (largest tiles
@@ -301,6 +301,11 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
     if (p->block_size) pl->block_size = p->block_size;
     if (p->keys_per_thread) pl->keys_per_thread = p->keys_per_thread;
     if (p->insertion_threshold) pl->insertion_threshold = p->insertion_threshold;
+    if (p->seg_block_cap) pl->seg_block_cap = p->seg_block_cap;
+    if (pl->seg_block_cap < 256 || pl->seg_block_cap > (w == 4 ? 8192 : 4096)) {
+        *err = "params.seg_block_cap must be in [256, 8192] (32-bit keys) or [256, 4096] (64-bit keys)";
+        return EVOSORT_ERR_INVALID;
+    }
     if (p->rank_mode) pl->rank_mode = p->rank_mode;
     else if (pl->digit_bits > 8) pl->rank_mode = 2;   // match masks are compiled for d <= 8
     if (pl->algo != EVOSORT_ALGO_RADIX && pl->algo != EVOSORT_ALGO_MERGE) {
@@ -442,6 +447,49 @@ evosort_status evosort_sort_pairs_to(const void* keys_in, const uint32_t* values
                                      const evosort_params* p) {
     if (n && (!values_in || !values_out)) return finish(EVOSORT_ERR_INVALID, "null value pointer");
     return sort_common(keys_in, keys_out, values_in, values_out, n, dt, p);
+}
+
+size_t evosort_segmented_workspace_bytes(size_t total, size_t nseg, evosort_dtype dt) {
+    if (!valid_dtype(dt)) return 0;
+    return segmented_workspace_bytes(total, nseg, dtype_bytes(dt));
+}
+
+evosort_status evosort_segmented_sort(void* keys, size_t total, const uint64_t* offsets, size_t nseg,
+                                      evosort_dtype dt, const evosort_params* p) {
+    std::string err;
+    set_error("");
+    if (!valid_dtype(dt)) return finish(EVOSORT_ERR_INVALID, "unknown dtype");
+    if (nseg == 0) return total == 0 ? EVOSORT_OK : finish(EVOSORT_ERR_INVALID, "total keys with no segments");
+    if (!offsets) return finish(EVOSORT_ERR_INVALID, "null offsets pointer");
+    if ((uintptr_t)offsets % 8) return finish(EVOSORT_ERR_INVALID, "misaligned offsets pointer");
+    const int w = dtype_bytes(dt);
+    if (total && !keys) return finish(EVOSORT_ERR_INVALID, "null key pointer");
+    if ((uintptr_t)keys % w) return finish(EVOSORT_ERR_INVALID, "misaligned key pointer");
+    if (nseg >= 0xFFFFFFFFull) return finish(EVOSORT_ERR_UNSUPPORTED, "nseg >= 2^32");
+    Plan pl;
+    int rc = resolve(p, dt, false, &pl, &err);
+    if (rc) return finish(rc, err);
+    cudaStream_t s = p ? (cudaStream_t)p->stream : nullptr;
+    const size_t need = segmented_workspace_bytes(total, nseg, w);
+    void* ws = p ? p->workspace : nullptr;
+    size_t ws_bytes = p ? p->workspace_bytes : 0;
+    bool owned = false;
+    if (!ws) {
+        const DevInfo* di = device_info(&err);
+        if (!di) return finish(EVOSORT_ERR_CUDA, err);
+        cudaError_t e = cudaMallocAsync(&ws, need, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return finish(EVOSORT_ERR_NOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+        }
+        ws_bytes = need;
+        owned = true;
+    } else if ((uintptr_t)ws % 256) {
+        return finish(EVOSORT_ERR_INVALID, "workspace must be 256-byte aligned");
+    }
+    rc = segmented_sort(keys, total, offsets, nseg, dt, pl, ws, ws_bytes, s, &err);
+    if (owned) cudaFreeAsync(ws, s);
+    return finish(rc, err);
 }
 
 evosort_status evosort_sync(void* stream) {

@@ -17,6 +17,7 @@ struct Plan {
     int keys_per_thread;      // keys each thread holds in a tile
     int insertion_threshold;  // mergesort base-run length
     int rank_mode;            // radix tile ranking variant
+    int seg_block_cap;        // segmented sort: longest segment sorted in shared memory
 };
 
 void set_error(const std::string& msg);
@@ -41,6 +42,10 @@ class ProfScope {
 size_t radix_workspace_bytes(size_t n, int w, bool pairs, const Plan& pl);
 int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt,
                const Plan& pl, void* ws, size_t ws_bytes, cudaStream_t s, std::string* err);
+
+size_t segmented_workspace_bytes(size_t total, size_t nseg, int w);
+int segmented_sort(void* keys, size_t total, const uint64_t* off, size_t nseg, int dt, const Plan& pl, void* ws,
+                   size_t ws_bytes, cudaStream_t s, std::string* err);
 
 size_t merge_workspace_bytes(size_t n, int w, bool pairs, const Plan& pl);
 int merge_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt,

@@ -22,6 +22,7 @@
 #include "evosort.h"
 #include "api_internal.h"
 #include "common.cuh"
+#include "smem_sort.cuh"
 
 namespace evosort {
 
@@ -44,22 +45,6 @@ struct MergeArgs {
     int btile;       // block-sort tile: tins * 2^m <= kMTile
 };
 
-// Merge-path split: number of keys of run A among the first k outputs of the
-// stable merge of A (length la) and B (length lb).
-template <typename U, typename AccA, typename AccB>
-__device__ __forceinline__ size_t merge_path(AccA A, size_t la, AccB B, size_t lb, size_t k) {
-    size_t lo = k > lb ? k - lb : 0;
-    size_t hi = k < la ? k : la;
-    while (lo < hi) {
-        const size_t mid = (lo + hi) >> 1;
-        if ((U)B(k - 1 - mid) < (U)A(mid))
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    return lo;
-}
-
 // ---------------------------------------------------------------------------
 // K4: block sort of one tile (base runs insertion-sorted, then merged).
 // ---------------------------------------------------------------------------
@@ -79,62 +64,10 @@ __global__ void __launch_bounds__(kMB) merge_block_sort(MergeArgs a, int dst_sel
         if (PAIRS) v0[i] = a.vin[base + i];
     }
     __syncthreads();
-    // insertion sort of each base run (Algorithm 3, InsertionSort on chunks)
-    const int runs = (len + a.tins - 1) / a.tins;
-    for (int r = threadIdx.x; r < runs; r += kMB) {
-        const int lo = r * a.tins;
-        const int hi = lo + a.tins < len ? lo + a.tins : len;
-        for (int i = lo + 1; i < hi; ++i) {
-            const U key = k0[i];
-            uint32_t val = PAIRS ? v0[i] : 0u;
-            int j = i;
-            while (j > lo && k0[j - 1] > key) {   // strictly greater: stable
-                k0[j] = k0[j - 1];
-                if (PAIRS) v0[j] = v0[j - 1];
-                --j;
-            }
-            k0[j] = key;
-            if (PAIRS) v0[j] = val;
-        }
-    }
-    __syncthreads();
-    // merge rounds inside the tile (MergeStandardOpt, currSize doubling)
-    const int chunk = (len + kMB - 1) / kMB;
-    U* ks = k0;
-    U* kd = k1;
-    uint32_t* vs = v0;
-    uint32_t* vd = v1;
-    for (int w = a.tins; w < len; w <<= 1) {
-        int o = threadIdx.x * chunk;
-        const int oend = o + chunk < len ? o + chunk : len;
-        while (o < oend) {
-            const int pbase = (o / (2 * w)) * (2 * w);
-            const int la = (pbase + w < len ? pbase + w : len) - pbase;
-            const int lb = (pbase + 2 * w < len ? pbase + 2 * w : len) - pbase - la;
-            const U* A = ks + pbase;
-            const U* B = A + la;
-            const int k = o - pbase;
-            int ia = (int)merge_path<U>([&](size_t i) { return A[i]; }, la, [&](size_t i) { return B[i]; }, lb,
-                                        (size_t)k);
-            int ib = k - ia;
-            const int stop = (pbase + la + lb < oend ? pbase + la + lb : oend);
-            for (; o < stop; ++o) {
-                const bool takeB = ia >= la || (ib < lb && B[ib] < A[ia]);
-                if (takeB) {
-                    kd[o] = B[ib];
-                    if (PAIRS) vd[o] = vs[pbase + la + ib];
-                    ++ib;
-                } else {
-                    kd[o] = A[ia];
-                    if (PAIRS) vd[o] = vs[pbase + ia];
-                    ++ia;
-                }
-            }
-        }
-        __syncthreads();
-        U* t = ks; ks = kd; kd = t;
-        uint32_t* tv = vs; vs = vd; vd = tv;
-    }
+    // insertion-sorted base runs, then the in-tile merge rounds (Algorithm 3)
+    const int which = smem_merge_sort<U, PAIRS>(k0, k1, v0, v1, len, a.tins);
+    const U* ks = which ? k1 : k0;
+    const uint32_t* vs = which ? v1 : v0;
     U* dst = dst_sel ? (U*)a.tmp : (U*)a.out;
     uint32_t* vdst = dst_sel ? a.vtmp : a.vout;
     for (int i = threadIdx.x; i < len; i += kMB) {
