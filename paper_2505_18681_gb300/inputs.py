@@ -257,7 +257,7 @@ def segmented_keys(lengths: torch.Tensor, dtype=torch.int32, seed: int = 42, dev
         seg = torch.searchsorted(offs_dev, i, right=True) - 1
         local = i - offs_dev[seg]
         r = raw64(st, s, c, device)
-        step = (1 << bits) // torch.clamp(lens_dev[seg], min=1)
+        step = ((1 << (bits - 2)) // torch.clamp(lens_dev[seg], min=1)) * 4   # ~2^bits / len, in int64
         ramp = local * step + lo
         replace = _bounded(raw64(aux, s, c, device), 100) == 0
         odd = (seg & 1) == 1

@@ -353,3 +353,17 @@ def test_planted_faults_are_caught(fault):
     finally:
         oracle.set_fault(0)
     assert _pins_pass()
+
+
+def test_segmented_generator_all_widths():
+    """The segmented-workload generator covers 32- and 64-bit keys."""
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    lens = inputs.segment_lengths(50, 16, 5000, seed=1)
+    for dt in (torch.int32, torch.int64, torch.uint32, torch.uint64):
+        keys, offs = inputs.segmented_keys(lens, dt, seed=1)
+        assert keys.numel() == int(offs[-1]) == int(lens.sum())
+        out = oracle.segmented_sort(keys.numpy(), offs.numpy().astype(np.uint64))
+        for i in range(0, 50, 7):
+            a, b = int(offs[i]), int(offs[i + 1])
+            assert np.array_equal(out[a:b], np.sort(keys.numpy()[a:b]))
