@@ -146,6 +146,28 @@ evosort_status evosort_segmented_sort(void* keys, size_t total, const uint64_t* 
 /* Scratch bytes evosort_segmented_sort needs for total keys in nseg segments. */
 size_t evosort_segmented_workspace_bytes(size_t total, size_t nseg, evosort_dtype dt);
 
+/* Keys-only sort that allocates no memory (the paper has no counterpart).
+ * For callers that may not allocate device memory where they sort: code
+ * running inside another framework's execute callback (a server plugin or a
+ * custom operator) whose host framework owns all device memory and forbids
+ * allocation calls, or latency-critical loops that must not block in the
+ * allocator.  Same result as evosort_sort_to with default parameters
+ * (LSD radix sort, Algorithms 4a/4b).  keys_in/keys_out: DEVICE arrays of n
+ * keys of dtype dt; they may be equal (in place) but must not otherwise
+ * overlap.  stream: cudaStream_t (NULL = legacy default stream).
+ * Scratch: a fixed 64 MiB buffer inside the library's device image, held by
+ * every device that loads the library until the process exits.  Sizes whose
+ * scratch exceeds it (about 7.4 million 64-bit or 15.7 million 32-bit keys) are
+ * rejected with EVOSORT_ERR_INVALID before anything is launched.
+ * The first call on each device looks up the buffer's device address (once,
+ * with that device current); make that first call before any stream capture.
+ * Every call on a device shares the one buffer: calls whose work overlaps on
+ * the GPU (different streams, or another thread) race and corrupt each other;
+ * order them on one stream.  The buffer keeps the last call's contents; the
+ * sort clears what it needs cleared itself. */
+evosort_status evosort_sort_noalloc(const void* keys_in, void* keys_out, size_t n, evosort_dtype dt,
+                                    void* stream);
+
 /* Waits for params-stream work (stream = NULL: the legacy default stream) and
  * returns the first error recorded on the device since the last call
  * (EVOSORT_ERR_TIMEOUT for a bounded wait that ran out), then clears it. */

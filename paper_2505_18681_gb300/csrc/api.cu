@@ -339,6 +339,14 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
 
 static bool valid_dtype(int dt) { return dt >= EVOSORT_I32 && dt <= EVOSORT_F64; }
 
+namespace evosort {
+// The built-in parameters of a keys-only radix sort of dtype dt.
+void default_radix_plan(int dt, Plan* pl) {
+    std::string err;
+    resolve(nullptr, dt, false, pl, &err);
+}
+}  // namespace evosort
+
 static bool overlaps(const void* a, const void* b, size_t bytes) {
     const char* x = (const char*)a;
     const char* y = (const char*)b;
