@@ -146,6 +146,93 @@ evosort_status evosort_segmented_sort(void* keys, size_t total, const uint64_t* 
 /* Scratch bytes evosort_segmented_sort needs for total keys in nseg segments. */
 size_t evosort_segmented_workspace_bytes(size_t total, size_t nseg, evosort_dtype dt);
 
+/* ---- Dispatcher and tuned table (Algorithm 5, AdaptivePartitionSort) ----
+ * With params == NULL or params->algo == EVOSORT_ALGO_AUTO and a non-empty
+ * table, a sort call classifies its input from a strided sample of 4096 keys
+ * (one small synchronous device-to-host copy on the call's stream) and uses
+ * the table entry for (dtype, size bucket = floor(log2 n), class): the nearest
+ * bucket of the same class, else of the RANDOM class, else the defaults.  The
+ * caller's stream and workspace are kept.  With an empty table nothing is
+ * sampled and the defaults are used. */
+typedef enum {
+    EVOSORT_CLASS_RANDOM = 0,    /* no structure found */
+    EVOSORT_CLASS_SKEWED = 1,    /* over a quarter of the keys share the top byte */
+    EVOSORT_CLASS_NARROW = 2,    /* at most half of the key bits vary (more than 16) */
+    EVOSORT_CLASS_FEW = 3,       /* at most 64 distinct values in the sample */
+    EVOSORT_CLASS_SORTED = 4,    /* >= 90% of sampled neighbours ascending */
+    EVOSORT_CLASS_REVERSE = 5,   /* >= 90% of sampled neighbours descending */
+    EVOSORT_CLASS_CONSTANT = 6,  /* one value */
+    EVOSORT_CLASS_NARROW16 = 7   /* at most 16 key bits vary */
+} evosort_dist_class;
+
+/* Class of keys[0..n) from a strided sample (synchronises the stream). */
+evosort_status evosort_classify(const void* keys, size_t n, evosort_dtype dt, void* stream, int* cls);
+
+/* Parameters the dispatcher would use for these keys; *cls receives the class
+ * (may be NULL).  Synchronises the stream when the table is not empty. */
+evosort_status evosort_plan(const void* keys, size_t n, evosort_dtype dt, void* stream, evosort_params* out,
+                            int* cls);
+
+/* Table of tuned parameters: set one entry (ms = its measured time, kept for
+ * reference), clear, count, save to / load from a text file (one entry per
+ * line: dtype size_bucket class algo digit_bits block_size keys_per_thread
+ * rank_mode insertion_threshold seg_block_cap ms; '#' starts a comment). */
+evosort_status evosort_table_set(evosort_dtype dt, int size_bucket, int cls, const evosort_params* p, float ms);
+void evosort_table_clear(void);
+size_t evosort_table_size(void);
+evosort_status evosort_table_save(const char* path);
+evosort_status evosort_table_load(const char* path);
+
+/* ---- Genetic-algorithm tuner (Algorithm 2, RunGATuning) ------------------
+ * Evolves the parameters of one sort of `sample` (a DEVICE array of n keys of
+ * dtype dt): algorithm (radix / merge, the paper's A_code), digit width,
+ * radix tile shape, ranking variant and insertion threshold.  Fitness is the
+ * median CUDA-event time of `reps` sorts; every genome's output is checked
+ * first, against `expected` bit for bit when given (a DEVICE array holding the
+ * sorted sample), else for sortedness and an order-free multiset fingerprint
+ * of the input; a failing genome gets +infinity.  The defaults genome is in
+ * the first generation, so the result is never slower than the defaults on
+ * the sample.  Writes the best genome's parameters to *best (stream set to
+ * `stream`), its time to *best_ms, and per generation best / mean / worst
+ * times to log[0 .. min(generations, log_cap)).  Allocates an output buffer
+ * of n keys from the stream-ordered pool; synchronises the stream. */
+typedef struct {
+    int population;          /* 30 (Section 4.2) */
+    int generations;         /* 10 */
+    double crossover_p;      /* 0.7: uniform crossover per parent pair */
+    double mutation_p;       /* 0.3: uniform mutation per individual */
+    double gene_mutation_p;  /* 0.2: each gene redrawn when mutating */
+    int elite;               /* 2: best genomes copied unchanged */
+    int tournament;          /* 3: tournament size of parent selection */
+    int reps;                /* 3: timings per genome (median) */
+    int tins_init_max;       /* 256: first-generation insertion threshold bound */
+    int allow_merge;         /* 1: the algorithm gene may pick mergesort */
+    uint64_t seed;           /* 42 */
+} evosort_ga_config;
+
+typedef struct {
+    int generation;
+    float best_ms, mean_ms, worst_ms;  /* over the genomes with a finite time */
+    int evaluations;                   /* distinct genomes timed so far */
+    evosort_params best;               /* best genome of the generation */
+} evosort_ga_log;
+
+void evosort_default_ga_config(evosort_ga_config* c);
+
+/* The GA loop alone, with the fitness supplied by the caller: fitness(p,
+ * best_so_far_ms (or -1 if none yet), ctx) returns the genome's time in ms,
+ * or a negative value for a failed genome.  evosort_tune runs it with a
+ * fitness that times the sort on the device; key_bytes (4 or 8) selects the
+ * default genome seeded into the first generation.  Deterministic for a given
+ * seed and fitness function. */
+typedef float (*evosort_fitness_fn)(const evosort_params* p, float best_so_far_ms, void* ctx);
+evosort_status evosort_ga_search(const evosort_ga_config* cfg, int key_bytes, evosort_fitness_fn fitness,
+                                 void* ctx, evosort_params* best, float* best_ms, evosort_ga_log* log,
+                                 int log_cap);
+evosort_status evosort_tune(const void* sample, size_t n, evosort_dtype dt, const void* expected,
+                            const evosort_ga_config* cfg, void* stream, evosort_params* best, float* best_ms,
+                            evosort_ga_log* log, int log_cap);
+
 /* Keys-only sort that allocates no memory (the paper has no counterpart).
  * For callers that may not allocate device memory where they sort: code
  * running inside another framework's execute callback (a server plugin or a

@@ -47,6 +47,29 @@ class Params(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t)]
 
 
+class GAConfig(ctypes.Structure):
+    """Mirror of ``evosort_ga_config``."""
+    _fields_ = [("population", ctypes.c_int), ("generations", ctypes.c_int), ("crossover_p", ctypes.c_double),
+                ("mutation_p", ctypes.c_double), ("gene_mutation_p", ctypes.c_double), ("elite", ctypes.c_int),
+                ("tournament", ctypes.c_int), ("reps", ctypes.c_int), ("tins_init_max", ctypes.c_int),
+                ("allow_merge", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class GALog(ctypes.Structure):
+    """Mirror of ``evosort_ga_log``."""
+    _fields_ = [("generation", ctypes.c_int), ("best_ms", ctypes.c_float), ("mean_ms", ctypes.c_float),
+                ("worst_ms", ctypes.c_float), ("evaluations", ctypes.c_int), ("best", Params)]
+
+
+FitnessFn = ctypes.CFUNCTYPE(ctypes.c_float, ctypes.POINTER(Params), ctypes.c_float, ctypes.c_void_p)
+
+CLASSES = {0: "random", 1: "skewed", 2: "narrow", 3: "few", 4: "sorted", 5: "reverse", 6: "constant",
+           7: "narrow16"}
+CLASS_CODE = {v: k for k, v in CLASSES.items()}
+PARAM_FIELDS = ("algo", "digit_bits", "keys_per_thread", "block_size", "insertion_threshold", "rank_mode",
+                "seg_block_cap")
+
+
 class KernelRecord(ctypes.Structure):
     """Mirror of ``evosort_kernel_record``."""
     _fields_ = [("kind", ctypes.c_int), ("pass_", ctypes.c_int), ("active", ctypes.c_int),
@@ -85,6 +108,28 @@ def library():
             lib.evosort_segmented_sort.restype = st
             lib.evosort_segmented_workspace_bytes.argtypes = [sz, sz, i]
             lib.evosort_segmented_workspace_bytes.restype = sz
+            lib.evosort_classify.argtypes = [vp, sz, i, vp, ctypes.POINTER(ctypes.c_int)]
+            lib.evosort_classify.restype = st
+            lib.evosort_plan.argtypes = [vp, sz, i, vp, pp, ctypes.POINTER(ctypes.c_int)]
+            lib.evosort_plan.restype = st
+            lib.evosort_table_set.argtypes = [i, i, i, pp, ctypes.c_float]
+            lib.evosort_table_set.restype = st
+            lib.evosort_table_clear.argtypes = []
+            lib.evosort_table_clear.restype = None
+            lib.evosort_table_size.argtypes = []
+            lib.evosort_table_size.restype = sz
+            lib.evosort_table_save.argtypes = [ctypes.c_char_p]
+            lib.evosort_table_save.restype = st
+            lib.evosort_table_load.argtypes = [ctypes.c_char_p]
+            lib.evosort_table_load.restype = st
+            lib.evosort_default_ga_config.argtypes = [ctypes.POINTER(GAConfig)]
+            lib.evosort_default_ga_config.restype = None
+            lib.evosort_tune.argtypes = [vp, sz, i, vp, ctypes.POINTER(GAConfig), vp, pp,
+                                         ctypes.POINTER(ctypes.c_float), ctypes.POINTER(GALog), i]
+            lib.evosort_tune.restype = st
+            lib.evosort_ga_search.argtypes = [ctypes.POINTER(GAConfig), i, FitnessFn, vp, pp,
+                                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(GALog), i]
+            lib.evosort_ga_search.restype = st
             lib.evosort_sync.argtypes = [vp]
             lib.evosort_sync.restype = st
             lib.evosort_last_error.argtypes = []
@@ -124,6 +169,8 @@ def _need_cuda(*ts):
 
 def _stream_handle(stream) -> int:
     if stream is None:
+        if not torch.cuda.is_available():
+            return 0   # host-only calls (tables, argument checks): the legacy default stream
         stream = torch.cuda.current_stream()
     if isinstance(stream, int):
         return stream
@@ -227,3 +274,95 @@ def profile_read() -> list:
     n = int(lib.evosort_profile_read(buf, cap))
     return [{"kind": KERNEL_KINDS.get(r.kind, r.kind), "pass": r.pass_, "active": bool(r.active),
              "ms": float(r.ms), "bytes": float(r.bytes), "items": int(r.items)} for r in buf[:min(n, cap)]]
+
+
+def params_dict(p: Params) -> dict:
+    """The tunable fields of a Params struct as a dict."""
+    return {f: int(getattr(p, f)) for f in PARAM_FIELDS}
+
+
+def classify(keys: torch.Tensor, stream=None) -> str:
+    """Distribution class of ``keys`` from a strided sample (synchronises)."""
+    _need_cuda(keys)
+    c = ctypes.c_int(0)
+    _check(library().evosort_classify(keys.data_ptr(), keys.numel(), _dtype_code(keys), _stream_handle(stream),
+                                      ctypes.byref(c)))
+    return CLASSES[c.value]
+
+
+def plan(keys: torch.Tensor, stream=None):
+    """(params dict, class) the dispatcher would use for ``keys``."""
+    _need_cuda(keys)
+    p = Params()
+    c = ctypes.c_int(0)
+    _check(library().evosort_plan(keys.data_ptr(), keys.numel(), _dtype_code(keys), _stream_handle(stream),
+                                  ctypes.byref(p), ctypes.byref(c)))
+    return params_dict(p), CLASSES[c.value]
+
+
+def table_set(dtype: torch.dtype, size_bucket: int, cls: str, params: dict, ms: float = 0.0) -> None:
+    p = make_params(**{k: v for k, v in params.items() if k != "algo"}, algo=params.get("algo", 0))
+    _check(library().evosort_table_set(DTYPES[dtype], int(size_bucket), CLASS_CODE[cls], ctypes.byref(p),
+                                       float(ms)))
+
+
+def table_clear() -> None:
+    library().evosort_table_clear()
+
+
+def table_size() -> int:
+    return int(library().evosort_table_size())
+
+
+def table_save(path: str) -> None:
+    _check(library().evosort_table_save(path.encode()))
+
+
+def table_load(path: str) -> None:
+    _check(library().evosort_table_load(path.encode()))
+
+
+def tune(sample: torch.Tensor, expected: torch.Tensor | None = None, stream=None, **ga):
+    """Runs the genetic algorithm on one device sample.  Returns
+    (best params dict, best ms, per-generation log as a list of dicts).
+    ``ga`` overrides fields of the default GA configuration."""
+    _need_cuda(sample, expected)
+    lib = library()
+    cfg = GAConfig()
+    lib.evosort_default_ga_config(ctypes.byref(cfg))
+    for k, v in ga.items():
+        setattr(cfg, k, v)
+    best = Params()
+    best_ms = ctypes.c_float(0)
+    logs = (GALog * max(cfg.generations, 1))()
+    _check(lib.evosort_tune(sample.data_ptr(), sample.numel(), _dtype_code(sample),
+                            expected.data_ptr() if expected is not None else None, ctypes.byref(cfg),
+                            _stream_handle(stream), ctypes.byref(best), ctypes.byref(best_ms), logs,
+                            cfg.generations))
+    log = [{"generation": g.generation, "best_ms": g.best_ms, "mean_ms": g.mean_ms, "worst_ms": g.worst_ms,
+            "evaluations": g.evaluations, "best": params_dict(g.best)} for g in logs[:cfg.generations]]
+    return params_dict(best), float(best_ms.value), log
+
+
+def ga_search(fitness, key_bytes: int = 8, **ga):
+    """The GA loop with a Python fitness function ``fitness(params_dict,
+    best_so_far_ms) -> ms`` (negative = failed genome).  Returns (best params
+    dict, best ms, log)."""
+    lib = library()
+    cfg = GAConfig()
+    lib.evosort_default_ga_config(ctypes.byref(cfg))
+    for k, v in ga.items():
+        setattr(cfg, k, v)
+
+    def cb(pp, best_so_far, _ctx):
+        return float(fitness(params_dict(pp.contents), float(best_so_far)))
+
+    fn = FitnessFn(cb)
+    best = Params()
+    best_ms = ctypes.c_float(0)
+    logs = (GALog * max(cfg.generations, 1))()
+    _check(lib.evosort_ga_search(ctypes.byref(cfg), int(key_bytes), fn, None, ctypes.byref(best),
+                                 ctypes.byref(best_ms), logs, cfg.generations))
+    log = [{"generation": g.generation, "best_ms": g.best_ms, "mean_ms": g.mean_ms, "worst_ms": g.worst_ms,
+            "evaluations": g.evaluations, "best": params_dict(g.best)} for g in logs[:cfg.generations]]
+    return params_dict(best), float(best_ms.value), log

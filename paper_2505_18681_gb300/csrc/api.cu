@@ -377,6 +377,19 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
         return finish(EVOSORT_ERR_INVALID, "keys and values must both be in place or both out of place");
     if (n >= (1ull << 40)) return finish(EVOSORT_ERR_UNSUPPORTED, "n >= 2^40");
     if (pairs && n > 0xFFFFFFFFull) return finish(EVOSORT_ERR_UNSUPPORTED, "key/value sorts need n < 2^32");
+    // dispatcher: tuned parameters for this input when the caller leaves the choice open
+    evosort_params planned;
+    if ((!p || p->algo == EVOSORT_ALGO_AUTO) && table_nonempty()) {
+        void* st = p ? p->stream : nullptr;
+        const evosort_status ps = evosort_plan(in, n, dt, st, &planned, nullptr);
+        if (ps != EVOSORT_OK) return finish(ps, evosort_last_error());
+        if (p) {
+            planned.stream = p->stream;
+            planned.workspace = p->workspace;
+            planned.workspace_bytes = p->workspace_bytes;
+        }
+        p = &planned;
+    }
     Plan pl;
     int rc = resolve(p, dt, pairs, &pl, &err);
     if (rc) return finish(rc, err);

@@ -22,6 +22,7 @@ struct Plan {
 
 void set_error(const std::string& msg);
 void default_radix_plan(int dt, Plan* pl);
+bool table_nonempty();
 void count_launches(uint64_t k);
 int sm_count();
 uint32_t* status_word(std::string* err);

@@ -1,0 +1,225 @@
+// Dispatcher of Algorithm 5 (AdaptivePartitionSort): picks the algorithm and
+// its parameters for one call from a table of tuned parameters, keyed by key
+// type, size bucket (floor(log2 n)) and a distribution class read off a small
+// strided sample of the keys.  The paper keys its parameters on n alone (one
+// GA run per size); the class adds what the data itself changes on a GPU:
+// which digits are constant, how many lanes of a warp share a digit.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "evosort.h"
+#include "api_internal.h"
+#include "common.cuh"
+
+namespace evosort {
+namespace {
+
+struct Entry {
+    int dt, bucket, cls;
+    evosort_params p;
+    float ms;
+};
+std::mutex g_tab_mu;
+std::vector<Entry> g_tab;
+
+constexpr int kSample = 4096;
+
+uint64_t host_map(uint64_t u, int dt) {
+    // order-preserving map of key bits, host copy (same definition as the kernels')
+    const int w = dtype_bytes(dt);
+    const KeyMap m = key_map_for(dt);
+    if (w == 4) {
+        const uint32_t x = (uint32_t)u;
+        const uint32_t sar = (x & 0x80000000u) ? 0xFFFFFFFFu : 0u;
+        return (uint32_t)((x ^ ((sar & (uint32_t)m.f) | (uint32_t)m.s)) - (uint32_t)m.r);
+    }
+    const uint64_t sar = (u >> 63) ? ~0ull : 0ull;
+    return (u ^ ((sar & m.f) | m.s)) - m.r;
+}
+
+}  // namespace
+
+bool table_nonempty() {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    return !g_tab.empty();
+}
+
+}  // namespace evosort
+
+using namespace evosort;
+
+extern "C" {
+
+evosort_status evosort_classify(const void* keys, size_t n, evosort_dtype dt, void* stream, int* cls) {
+    set_error("");
+    if (!cls || (n && !keys) || dt < EVOSORT_I32 || dt > EVOSORT_F64) {
+        set_error("evosort_classify: bad argument");
+        return EVOSORT_ERR_INVALID;
+    }
+    const int w = dtype_bytes(dt);
+    if (n < 2) {
+        *cls = EVOSORT_CLASS_CONSTANT;
+        return EVOSORT_OK;
+    }
+    const size_t m = n < (size_t)kSample ? n : (size_t)kSample;
+    const size_t stride = n / m;
+    std::vector<uint64_t> raw(m, 0);
+    std::vector<unsigned char> buf(m * w);
+    // one strided device-to-host copy of m keys
+    cudaError_t e = cudaMemcpy2DAsync(buf.data(), w, keys, stride * w, w, m, cudaMemcpyDeviceToHost,
+                                      (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("evosort_classify: sample copy: ") + cudaGetErrorString(e));
+        return EVOSORT_ERR_CUDA;
+    }
+    for (size_t i = 0; i < m; ++i) {
+        uint64_t u = 0;
+        std::memcpy(&u, buf.data() + i * w, w);
+        raw[i] = host_map(u, dt);
+    }
+    size_t asc = 0, desc = 0;
+    uint64_t vary = 0;
+    for (size_t i = 0; i + 1 < m; ++i) {
+        asc += raw[i] <= raw[i + 1];
+        desc += raw[i] >= raw[i + 1];
+    }
+    for (size_t i = 0; i < m; ++i) vary |= raw[i] ^ raw[0];
+    std::vector<uint64_t> sorted(raw);
+    std::sort(sorted.begin(), sorted.end());
+    const size_t distinct = std::unique(sorted.begin(), sorted.end()) - sorted.begin();
+    // top-byte concentration: share of the sample in the most common top byte
+    size_t top[256] = {0};
+    for (size_t i = 0; i < m; ++i) top[(raw[i] >> (8 * w - 8)) & 0xFF] += 1;
+    const size_t topmax = *std::max_element(top, top + 256);
+    int bits = 0;
+    while (bits < 64 && (vary >> bits)) ++bits;
+    int c;
+    if (distinct == 1) c = EVOSORT_CLASS_CONSTANT;
+    else if (asc >= (size_t)(0.9 * (m - 1)) && asc > desc) c = EVOSORT_CLASS_SORTED;
+    else if (desc >= (size_t)(0.9 * (m - 1))) c = EVOSORT_CLASS_REVERSE;
+    else if (distinct <= 64) c = EVOSORT_CLASS_FEW;
+    else if (bits <= 16) c = EVOSORT_CLASS_NARROW16;
+    else if (bits <= 4 * w) c = EVOSORT_CLASS_NARROW;          // at most half the key bits vary
+    else if (topmax * 4 > m) c = EVOSORT_CLASS_SKEWED;         // a quarter in one top byte
+    else c = EVOSORT_CLASS_RANDOM;
+    *cls = c;
+    return EVOSORT_OK;
+}
+
+evosort_status evosort_table_set(evosort_dtype dt, int size_bucket, int cls, const evosort_params* p, float ms) {
+    if (!p || dt < EVOSORT_I32 || dt > EVOSORT_F64 || size_bucket < 0 || size_bucket > 63 || cls < 0 ||
+        cls > EVOSORT_CLASS_NARROW16) {
+        set_error("evosort_table_set: bad argument");
+        return EVOSORT_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    Entry en{dt, size_bucket, cls, *p, ms};
+    en.p.stream = nullptr;
+    en.p.workspace = nullptr;
+    en.p.workspace_bytes = 0;
+    for (auto& x : g_tab)
+        if (x.dt == dt && x.bucket == size_bucket && x.cls == cls) {
+            x = en;
+            return EVOSORT_OK;
+        }
+    g_tab.push_back(en);
+    return EVOSORT_OK;
+}
+
+void evosort_table_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    g_tab.clear();
+}
+
+size_t evosort_table_size(void) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    return g_tab.size();
+}
+
+evosort_status evosort_table_save(const char* path) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    std::ofstream f(path ? path : "");
+    if (!f) {
+        set_error("evosort_table_save: cannot open file");
+        return EVOSORT_ERR_INVALID;
+    }
+    f << "# evosort tuned table: dtype size_bucket class algo digit_bits block_size keys_per_thread "
+         "rank_mode insertion_threshold seg_block_cap ms\n";
+    for (const auto& x : g_tab)
+        f << x.dt << ' ' << x.bucket << ' ' << x.cls << ' ' << x.p.algo << ' ' << x.p.digit_bits << ' '
+          << x.p.block_size << ' ' << x.p.keys_per_thread << ' ' << x.p.rank_mode << ' '
+          << x.p.insertion_threshold << ' ' << x.p.seg_block_cap << ' ' << x.ms << '\n';
+    return f ? EVOSORT_OK : EVOSORT_ERR_INVALID;
+}
+
+evosort_status evosort_table_load(const char* path) {
+    std::ifstream f(path ? path : "");
+    if (!f) {
+        set_error("evosort_table_load: cannot open file");
+        return EVOSORT_ERR_INVALID;
+    }
+    std::string line;
+    int lineno = 0;
+    while (std::getline(f, line)) {
+        ++lineno;
+        if (line.empty() || line[0] == '#') continue;
+        std::istringstream is(line);
+        int dt, bucket, cls;
+        evosort_params p;
+        evosort_default_params(&p);
+        float ms = 0;
+        if (!(is >> dt >> bucket >> cls >> p.algo >> p.digit_bits >> p.block_size >> p.keys_per_thread >>
+              p.rank_mode >> p.insertion_threshold >> p.seg_block_cap >> ms)) {
+            set_error("evosort_table_load: malformed line " + std::to_string(lineno));
+            return EVOSORT_ERR_INVALID;
+        }
+        const evosort_status st = evosort_table_set((evosort_dtype)dt, bucket, cls, &p, ms);
+        if (st != EVOSORT_OK) return st;
+    }
+    return EVOSORT_OK;
+}
+
+evosort_status evosort_plan(const void* keys, size_t n, evosort_dtype dt, void* stream, evosort_params* out,
+                            int* cls_out) {
+    set_error("");
+    if (!out) {
+        set_error("evosort_plan: null output");
+        return EVOSORT_ERR_INVALID;
+    }
+    evosort_default_params(out);
+    out->stream = stream;
+    int cls = EVOSORT_CLASS_RANDOM;
+    if (table_nonempty() && n >= 2) {
+        const evosort_status st = evosort_classify(keys, n, dt, stream, &cls);
+        if (st != EVOSORT_OK) return st;
+        int bucket = 0;
+        while (bucket < 63 && (n >> (bucket + 1))) ++bucket;
+        std::lock_guard<std::mutex> lk(g_tab_mu);
+        const Entry* best = nullptr;
+        int bestd = 1 << 30;
+        for (int pass = 0; pass < 2 && !best; ++pass) {   // the class itself, then the random class
+            const int want = pass == 0 ? cls : EVOSORT_CLASS_RANDOM;
+            for (const auto& x : g_tab)
+                if (x.dt == dt && x.cls == want && std::abs(x.bucket - bucket) < bestd) {
+                    best = &x;
+                    bestd = std::abs(x.bucket - bucket);
+                }
+        }
+        if (best) {
+            *out = best->p;
+            out->stream = stream;
+        }
+    }
+    if (cls_out) *cls_out = cls;
+    return EVOSORT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+"""GPU checks of the dispatcher (Algorithm 5) and the GA tuner (Algorithm 2)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def evo():
+    import paper_2505_18681_gb300 as evo
+    evo.library()
+    evo.table_clear()
+    yield evo
+    evo.table_clear()
+
+
+EXPECTED_CLASS = {"uniform": "random", "gaussian": "skewed", "sorted": "sorted", "reverse": "reverse",
+                  "nearly_sorted": "sorted", "distinct16": "few", "zipf": "narrow", "equal": "constant",
+                  "uniform1000": "narrow16"}
+
+
+@pytest.mark.parametrize("dist", list(EXPECTED_CLASS))
+def test_classify_workload_distributions(evo, dist):
+    from paper_2505_18681_gb300 import inputs
+    x = inputs.generate(dist, 1_000_003, torch.int64, seed=42, device="cuda")
+    assert evo.classify(x) == EXPECTED_CLASS[dist]
+
+
+def test_tune_small_sample_against_oracle(evo):
+    """The GA with the oracle's sorted sample as the reference: every winning
+    genome produced the exact answer; the log is consistent."""
+    from paper_2505_18681_gb300 import inputs
+    x = inputs.generate("gaussian", 1 << 20, torch.int64, seed=42, device="cuda")
+    expected = torch.from_numpy(oracle.radix_sort(x.cpu().numpy())).cuda()
+    best, ms, log = evo.tune(x, expected=expected, population=12, generations=4, reps=2, seed=1)
+    assert np.isfinite(ms) and ms > 0
+    bests = [g["best_ms"] for g in log]
+    assert all(b2 <= b1 + 1e-6 for b1, b2 in zip(bests, bests[1:]))
+    y = torch.empty_like(x)
+    evo.sort(x, out=y, **best)
+    evo.sync()
+    assert torch.equal(y, expected)
+
+
+def test_tune_without_reference_uses_device_checks(evo):
+    from paper_2505_18681_gb300 import inputs
+    x = inputs.generate("distinct16", 1 << 19, torch.int32, seed=3, device="cuda")
+    best, ms, _ = evo.tune(x, population=8, generations=2, reps=1, seed=2)
+    y = torch.empty_like(x)
+    evo.sort(x, out=y, **best)
+    evo.sync()
+    assert np.array_equal(y.cpu().numpy(), oracle.radix_sort(x.cpu().numpy()))
+
+
+def test_dispatcher_uses_table(evo):
+    from paper_2505_18681_gb300 import inputs
+    evo.table_clear()
+    evo.table_set(torch.int64, 19, "few", {"algo": 0, "digit_bits": 6, "block_size": 256,
+                                          "keys_per_thread": 16, "rank_mode": 2})
+    evo.table_set(torch.int64, 19, "random", {"algo": 1, "insertion_threshold": 24})
+    x = inputs.generate("distinct16", 700_001, torch.int64, seed=5, device="cuda")
+    p, cls = evo.plan(x)
+    assert cls == "few" and p["digit_bits"] == 6 and p["rank_mode"] == 2
+    u = inputs.generate("uniform", 600_001, torch.int64, seed=5, device="cuda")
+    p, cls = evo.plan(u)
+    assert cls == "random" and p["algo"] == 1 and p["insertion_threshold"] == 24
+    s = inputs.generate("sorted", 500_001, torch.int64, seed=5, device="cuda")
+    p, cls = evo.plan(s)                       # no "sorted" entry: falls back to "random"
+    assert cls == "sorted" and p["algo"] == 1
+    for t in (x, u, s):
+        y = torch.empty_like(t)
+        evo.sort(t, out=y)                    # params=None -> dispatcher
+        z = t.clone()
+        evo.sort(z, algo="auto")              # in place, algo auto
+        evo.sync()
+        e = oracle.radix_sort(t.cpu().numpy())
+        assert np.array_equal(y.cpu().numpy(), e) and np.array_equal(z.cpu().numpy(), e)
+    evo.table_clear()
+    p, cls = evo.plan(x)                      # empty table: defaults, no sampling
+    assert p["algo"] == 0 and p["digit_bits"] == 0
