@@ -253,6 +253,21 @@ def main():
     plain = [evo.make_params(algo="radix", stream=stream, **kw) for _ in dists]
     params = plain
     mode = "plain"
+    table = os.path.join(ROOT, "paper_2505_18681_gb300", "tuned", "gb300_%s.txt" % args.dtype)
+    plans = {}
+    if args.params in ("auto", "tuned") and not kw and os.path.exists(table):
+        # GA-tuned parameters per array, chosen by the dispatcher from each
+        # array's sampled distribution class (classified once, before timing)
+        evo.table_clear()
+        evo.table_load(table)
+        params = []
+        for d, x in zip(dists, xs):
+            pd, cls = evo.plan(x, stream=stream)
+            plans[d] = {"class": cls, **pd}
+            params.append(evo.make_params(stream=stream, **pd))
+        mode = "tuned"
+    elif args.params == "tuned":
+        raise SystemExit("no tuned table at %s" % table)
     # pre-size the scratch pool so the timed region allocates nothing new
     ws_bytes = max(evo.workspace_bytes(n, tdt, **kw), 1)
     pre = torch.empty(0)
@@ -294,6 +309,29 @@ def main():
         ms_step = float(t.item())
     keys_per_step = n * len(dists) * ws
     value = keys_per_step / (ms_step * 1e-3) / 1e9
+
+    # the plain arm (built-in defaults, one launch sequence per array) on the
+    # same inputs, for the tuned-vs-plain comparison
+    plain_line = None
+    if mode == "tuned":
+        for _ in range(max(args.warmup, 1)):
+            step(plain)
+        barrier()
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            step(plain)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / args.steps
+        if ws > 1:
+            t = torch.tensor([pms], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            pms = float(t.item())
+        plain_line = {"value": keys_per_step / (pms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": pms,
+                      "tuned_over_plain": pms / ms_step}
 
     # dominant kernel: the onesweep pass; time-weighted over active launches
     by_kind = {}
@@ -345,9 +383,11 @@ def main():
             "config": {"workload": "nine-distribution %s sort, %d keys per array (one step sorts all nine)"
                        % (args.dtype, n), "n_per_array": n, "dists": dists, "params": mode,
                        "param_overrides": kw,
+                       "tuned_plans": plans,
                        "l2": "inputs larger than L2 (%.1f GB per array), no flush" % (n * w / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "e2e": e2e,
+            "plain": plain_line,
             "roofline": {"bound": "hbm", "kernel": "radix_onesweep", "achieved": ach, "peak": peak,
                          "unit": "GB/s", "frac": ach / peak if peak else None, "traffic": traffic,
                          "peak_source": peak_src,
