@@ -67,6 +67,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device) -> float:
+    """Max of a per-rank value over all ranks (the step time every rank waits
+    for); the identity when no process group is running."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gkeys(keys_per_rank_step: int, world: int, ms_step: float) -> float:
+    """Whole-job throughput: keys of all ranks per step over the slowest rank's step time."""
+    return keys_per_rank_step * world / (ms_step * 1e-3) / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -302,13 +319,9 @@ def main():
     evo.profile(False)
     evo.sync(stream)
     ms = e0.elapsed_time(e1)
-    ms_step = ms / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_step], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms / args.steps, dev)
     keys_per_step = n * len(dists) * ws
-    value = keys_per_step / (ms_step * 1e-3) / 1e9
+    value = whole_job_gkeys(n * len(dists), ws, ms_step)
 
     # the plain arm (built-in defaults, one launch sequence per array) on the
     # same inputs, for the tuned-vs-plain comparison
@@ -325,11 +338,7 @@ def main():
             step(plain)
         p1.record(stream)
         torch.cuda.synchronize()
-        pms = p0.elapsed_time(p1) / args.steps
-        if ws > 1:
-            t = torch.tensor([pms], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            pms = float(t.item())
+        pms = max_over_ranks(p0.elapsed_time(p1) / args.steps, dev)
         plain_line = {"value": keys_per_step / (pms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": pms,
                       "tuned_over_plain": pms / ms_step}
 
@@ -431,12 +440,7 @@ def measure_e2e(evo, xs, out, params, stream, n, w, args, barrier, ws, dev):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    if ws > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dev)
     keys = n * len(xs) * ws
     return {"value": keys / (ms * 1e-3) / 1e9, "unit": "GKeys/s", "h2d_bytes_per_step": n * w * len(xs),
             "d2h_bytes_per_step": n * w * len(xs), "ms_per_step": ms, "steps": steps}
