@@ -216,8 +216,8 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     cudaError_t e = cudaMemsetAsync(base, 0, L.zero_end, s);
     const int sms = sm_count();
     const size_t hist_smem = (size_t)L.npass * ((size_t)1 << pl.digit_bits) * sizeof(uint32_t);
-    size_t hist_grid = (n + 512 * 16 - 1) / (512 * 16);
-    if (hist_grid > (size_t)sms * 4) hist_grid = (size_t)sms * 4;
+    size_t hist_grid = (n + 1024 * 16 - 1) / (1024 * 16);
+    if (hist_grid > (size_t)sms) hist_grid = (size_t)sms;   // one 1024-thread CTA per SM (128 KB counters)
     if (hist_grid < 1) hist_grid = 1;
     const int vb = pairs ? 4 : 0;
     const double pass_bytes = 2.0 * (double)n * (w + vb);

@@ -75,31 +75,45 @@ __device__ __forceinline__ uint32_t* sel_vdst(const RadixArgs& a, int s) {
 
 // ---------------------------------------------------------------------------
 // K1: digit histograms of every pass in one read of the keys.
-// Shared counters per CTA (npass << d of them).  Each thread reads a run of
-// HC consecutive keys and merges consecutive equal digits before the shared
-// atomic; when a whole warp ends its runs on the same digit (sorted and
-// low-entropy inputs) the warp adds one reduced count instead of 32.
+// Shared counters per CTA, replicated in `cols` columns (lane % cols): the
+// counter of (pass, digit, column) sits at ((pass * bins + digit) * cols +
+// column), so with 32 columns each lane only ever touches its own bank and
+// the shared atomics never conflict.  Each thread reads a run of HC
+// consecutive keys and merges consecutive equal digits before the atomic;
+// when a whole warp ends its runs on one digit (sorted and low-entropy input)
+// the warp adds one reduced count instead of 32.
 // ---------------------------------------------------------------------------
-template <typename U>
-__device__ __forceinline__ void hist_add_run(uint32_t* h, uint32_t dig, uint32_t run, bool warp_full) {
+constexpr int kHistThreads = 1024;
+constexpr size_t kHistSmem = 128 * 1024;
+
+// columns of the histogram for a pass count and digit width (power of two)
+__host__ __device__ constexpr int hist_cols(int npass, int d) {
+    int c = 32;
+    while (c > 1 && (size_t)npass * ((size_t)1 << d) * c * 4 > kHistSmem) c >>= 1;
+    return c;
+}
+
+__device__ __forceinline__ void hist_add_run(uint32_t* h, int cols, uint32_t dig, uint32_t run, bool warp_full) {
+    const int lane = threadIdx.x & 31;
     if (warp_full) {
         const uint32_t d0 = __shfl_sync(0xffffffffu, dig, 0);
         if (__all_sync(0xffffffffu, dig == d0)) {
             const uint32_t t = __reduce_add_sync(0xffffffffu, run);
-            if ((threadIdx.x & 31) == 0) atomicAdd(&h[d0], t);
+            if (lane == 0) atomicAdd(&h[d0 * cols], t);
             return;
         }
     }
-    atomicAdd(&h[dig], run);
+    atomicAdd(&h[dig * cols + (lane & (cols - 1))], run);
 }
 
 template <typename U>
-__global__ void __launch_bounds__(512) radix_histogram(RadixArgs a) {
+__global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
     extern __shared__ uint32_t s_h[];
     const int bins = 1 << a.d;
+    const int cols = hist_cols(a.npass, a.d);
     const int total = a.npass * bins;
     const uint32_t mask = (uint32_t)(bins - 1);
-    for (int i = threadIdx.x; i < total; i += blockDim.x) s_h[i] = 0;
+    for (int i = threadIdx.x; i < total * cols; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
 
     constexpr int V = 16 / sizeof(U);   // keys per 128-bit load
@@ -107,6 +121,8 @@ __global__ void __launch_bounds__(512) radix_histogram(RadixArgs a) {
     const U* keys = (const U*)a.in;
     const size_t n = a.n;
     const KeyMap map = a.map;
+    const int lane = threadIdx.x & 31;
+    const int col = lane & (cols - 1);
     // 16-byte aligned body of whole runs; the head and tail use scalar loads
     size_t head = ((16 - ((uintptr_t)keys & 15)) & 15) / sizeof(U);
     if (head > n) head = n;
@@ -117,7 +133,8 @@ __global__ void __launch_bounds__(512) radix_histogram(RadixArgs a) {
 
     auto count_key = [&](U k) {
         k = map_fwd(k, map);
-        for (int p = 0; p < a.npass; ++p) atomicAdd(&s_h[p * bins + digit_of(k, p * a.d, mask)], 1u);
+        for (int p = 0; p < a.npass; ++p)
+            atomicAdd(&s_h[(p * bins + digit_of(k, p * a.d, mask)) * cols + col], 1u);
     };
     if (gtid < head) count_key(keys[gtid]);
     if (gtid < n - tail0) count_key(keys[tail0 + gtid]);
@@ -125,7 +142,6 @@ __global__ void __launch_bounds__(512) radix_histogram(RadixArgs a) {
     // warps take 32 consecutive runs at a time, one run per lane
     const size_t warp_id = gtid >> 5;
     const size_t nwarps = gthreads >> 5;
-    const int lane = threadIdx.x & 31;
     for (size_t r0 = warp_id * 32; r0 < nruns; r0 += nwarps * 32) {
         const size_t r = r0 + lane;
         const bool warp_full = r0 + 32 <= nruns;
@@ -141,7 +157,7 @@ __global__ void __launch_bounds__(512) radix_histogram(RadixArgs a) {
             for (int j = 0; j < HC; ++j) k[j] = map_fwd(k[j], map);
             for (int p = 0; p < a.npass; ++p) {
                 const int sh = p * a.d;
-                uint32_t* h = s_h + p * bins;
+                uint32_t* h = s_h + (size_t)p * bins * cols;
                 uint32_t cur = digit_of(k[0], sh, mask);
                 uint32_t run = 1;
 #pragma unroll
@@ -150,18 +166,21 @@ __global__ void __launch_bounds__(512) radix_histogram(RadixArgs a) {
                     if (dg == cur) {
                         ++run;
                     } else {
-                        atomicAdd(&h[cur], run);
+                        atomicAdd(&h[cur * cols + col], run);
                         cur = dg;
                         run = 1;
                     }
                 }
-                hist_add_run<U>(h, cur, run, warp_full);
+                hist_add_run(h, cols, cur, run, warp_full);
             }
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < total; i += blockDim.x)
-        if (s_h[i]) atomicAdd(&a.counts[i], (unsigned long long)s_h[i]);
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        uint32_t sum = 0;
+        for (int c = 0; c < cols; ++c) sum += s_h[i * cols + ((c + i) & (cols - 1))];
+        if (sum) atomicAdd(&a.counts[i], (unsigned long long)sum);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -20,10 +20,20 @@ cudaError_t launch_onesweep_u64(bool pairs, int block, int kpt, int rank, size_t
 cudaError_t launch_radix_aux(int w, int which, size_t grid, size_t smem, cudaStream_t s, const RadixArgs& a,
                              int inplace) {
     if (which == 0) {
+        static bool configured = false;
+        if (!configured) {
+            cudaFuncSetAttribute(radix_histogram<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHistSmem);
+            cudaFuncSetAttribute(radix_histogram<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHistSmem);
+            configured = true;
+        }
+        (void)smem;
+        const size_t hs = (size_t)a.npass * ((size_t)1 << a.d) * hist_cols(a.npass, a.d) * 4;
         if (w == 4)
-            radix_histogram<uint32_t><<<(unsigned)grid, 512, smem, s>>>(a);
+            radix_histogram<uint32_t><<<(unsigned)grid, kHistThreads, hs, s>>>(a);
         else
-            radix_histogram<uint64_t><<<(unsigned)grid, 512, smem, s>>>(a);
+            radix_histogram<uint64_t><<<(unsigned)grid, kHistThreads, hs, s>>>(a);
     } else if (which == 1) {
         radix_scan_plan<<<1, 1024, 0, s>>>(a, inplace);
     } else {

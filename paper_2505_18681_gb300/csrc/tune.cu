@@ -51,8 +51,8 @@ struct Rng {
     int range(int lo, int hi) { return lo + (int)(next() % (uint64_t)(hi - lo + 1)); }
 };
 
-const int kShapes[][2] = {{256, 16}, {512, 16}, {512, 32}, {1024, 8}, {1024, 16}};
-constexpr int kNShapes = 5;
+const int kShapes[][2] = {{256, 16}, {512, 16}, {512, 32}, {1024, 8}, {1024, 16}, {512, 8}};
+constexpr int kNShapes = 6;
 
 struct Genome {
     int algo, d, shape, rank, tins;

@@ -106,7 +106,7 @@ def tile_fits(block, kpt, w, pairs, d, rank):
     return smem <= 232448 - 1024
 
 
-@pytest.mark.parametrize("shape", [(256, 16), (512, 16), (512, 32), (1024, 8), (1024, 16)])
+@pytest.mark.parametrize("shape", [(256, 16), (512, 8), (512, 16), (512, 32), (1024, 8), (1024, 16)])
 @pytest.mark.parametrize("rank", [1, 2, 3])
 @pytest.mark.parametrize("d", [6, 8, 11])
 def test_tile_shapes_and_ranking(evo, shape, rank, d):
