@@ -123,11 +123,12 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
     const KeyMap map = a.map;
     const int lane = threadIdx.x & 31;
     const int col = lane & (cols - 1);
-    // 16-byte aligned body of whole runs; the head and tail use scalar loads
+    // 16-byte aligned body of whole warp chunks (32 runs of HC keys); the
+    // head and the tail use scalar loads
     size_t head = ((16 - ((uintptr_t)keys & 15)) & 15) / sizeof(U);
     if (head > n) head = n;
-    const size_t nruns = (n - head) / HC;
-    const size_t tail0 = head + nruns * HC;
+    const size_t nchunks = (n - head) / (32 * HC);
+    const size_t tail0 = head + nchunks * 32 * HC;
     const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t gthreads = (size_t)gridDim.x * blockDim.x;
 
@@ -139,18 +140,19 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
     if (gtid < head) count_key(keys[gtid]);
     if (gtid < n - tail0) count_key(keys[tail0 + gtid]);
 
-    // warps take 32 consecutive runs at a time, one run per lane
+    // warps take 32 runs (32 * HC consecutive keys) at a time; lane L reads
+    // the 16-byte vectors L, L + 32, ... of the warp's chunk, so every load
+    // instruction covers 512 contiguous bytes
     const size_t warp_id = gtid >> 5;
     const size_t nwarps = gthreads >> 5;
-    for (size_t r0 = warp_id * 32; r0 < nruns; r0 += nwarps * 32) {
-        const size_t r = r0 + lane;
-        const bool warp_full = r0 + 32 <= nruns;
-        if (r < nruns) {
+    for (size_t c = warp_id; c < nchunks; c += nwarps) {
+        const bool warp_full = true;
+        {
             U k[HC];
-            const uint4* vp = (const uint4*)(keys + head + r * HC);
+            const uint4* vp = (const uint4*)(keys + head + c * 32 * HC);
 #pragma unroll
             for (int j = 0; j < HC / V; ++j) {
-                const uint4 v = vp[j];
+                const uint4 v = __ldcs(vp + j * 32 + lane);
                 memcpy(&k[j * V], &v, 16);
             }
 #pragma unroll
@@ -274,11 +276,11 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t dig) {
 
 // Dynamic shared memory of one onesweep CTA: three tile buffers (two TMA
 // input buffers, one reorder buffer), per-warp digit counters, the tile's
-// digit offsets and global bases, two mbarriers.  (Rank mode 3 keeps its
+// digit offsets, counts and global bases, two mbarriers.  (Rank mode 3 keeps its
 // per-warp match masks in the reorder buffer.)
 __host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d, int rank) {
     return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * ((size_t)1 << d) * 2 +
-           ((size_t)1 << d) * 12 + 16;
+           ((size_t)1 << d) * 16 + 16;
 }
 // Largest dynamic shared memory a CTA may use on sm_100-class GPUs (227 KB),
 // less room for the kernel's static shared variables.
@@ -328,6 +330,78 @@ __device__ __forceinline__ uint64_t lookback_digit(const S* slot0, size_t stride
     return excl;
 }
 
+// Decoupled look-back for one digit by a pair of adjacent lanes: the lane
+// with q = 0 reads the 16 nearest unread predecessors, q = 1 the 16 beyond, so
+// one L2 round trip covers 32 tiles.  Both lanes return the same sum.
+template <typename S>
+__device__ __forceinline__ uint64_t lookback_pair(const S* slot0, size_t stride, long long tile,
+                                                  uint32_t* status) {
+    constexpr int FB = sizeof(S) * 8 - 2;
+    const S cmask = ((S)1 << FB) - 1;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & 1;
+    const unsigned pm = 3u << (lane & ~1);
+    uint64_t excl = 0;
+    long long t0 = tile - 1;
+    uint32_t polls = 0;
+    for (;;) {
+        S v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const long long t = t0 - q * 16 - i;
+            v[i] = t >= 0 ? ld_relaxed(slot0 + (size_t)t * stride) : ((S)2 << FB);
+        }
+        uint64_t sum = 0;
+        int adv = 0;
+        bool fin = false, blk = false;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (!fin && !blk) {
+                const uint32_t f = (uint32_t)(v[i] >> FB);
+                if (f == 0) {
+                    blk = true;
+                } else {
+                    sum += (uint64_t)(v[i] & cmask);
+                    ++adv;
+                    if (f == 2) fin = true;
+                }
+            }
+        }
+        const int st = adv | (fin ? 64 : 0) | (blk ? 128 : 0);
+        const uint64_t sum0 = __shfl_sync(pm, sum, lane & ~1);
+        const uint64_t sum1 = __shfl_sync(pm, sum, lane | 1);
+        const int st0 = __shfl_sync(pm, st, lane & ~1);
+        const int st1 = __shfl_sync(pm, st, lane | 1);
+        bool waiting = false;
+        if (st0 & 64) {                    // inclusive prefix among the near 16
+            excl += sum0;
+            break;
+        } else if (st0 & 128) {            // near window blocked on an unpublished tile
+            excl += sum0;
+            t0 -= st0 & 63;
+            waiting = true;
+        } else {                           // near 16 were aggregates: go on with the far 16
+            excl += sum0 + sum1;
+            if (st1 & 64) break;
+            if (st1 & 128) {
+                t0 -= 16 + (st1 & 63);
+                waiting = true;
+            } else {
+                t0 -= 32;
+            }
+        }
+        if (waiting) {
+            if (++polls > kSpinLimit) {
+                atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+            if ((polls & 255u) == 0 && ld_relaxed(status) != 0) break;
+            __nanosleep(32);
+        }
+    }
+    return excl;
+}
+
 // CTAs per SM the register budget is tuned for: about 40 registers plus one
 // per key of the thread.
 constexpr int onesweep_min_blocks(int block, int kpt) {
@@ -356,7 +430,8 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     uint32_t* s_rvals = (uint32_t*)(smem + 2 * (KB + VB) + KB);
     uint16_t* s_whist = (uint16_t*)(smem + 3 * (KB + VB));
     uint32_t* s_excl = (uint32_t*)(s_whist + WARPS * bins);
-    unsigned long long* s_gbase = (unsigned long long*)(s_excl + bins);
+    uint32_t* s_tcnt = s_excl + bins;
+    unsigned long long* s_gbase = (unsigned long long*)(s_tcnt + bins);
     uint64_t* s_bar = (uint64_t*)(s_gbase + bins);
     // RANK 3 match masks (WARPS x bins words) live in the reorder buffer,
     // which is idle while a tile is ranked
@@ -485,6 +560,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                 }
                 cnt[j] = s;
                 mysum += s;
+                s_tcnt[b] = s;
                 const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
                 if (a.lb64)
                     st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | s);
@@ -521,7 +597,30 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         // ---- decoupled look-back for the owned digits.  No barrier follows:
         // threads without digits to resolve go straight on to the reorder,
         // which overlaps the look-back's L2 round trips.
-        {
+        if (2 * bins <= BLOCK) {
+            // two lanes per digit, warps [0, 2 * bins / 32); the other warps
+            // start the reorder at once
+            if (tid < 2 * bins) {
+                const int b = tid >> 1;
+                const unsigned long long* boff = a.counts + (size_t)pass * bins;
+                const size_t slot0 = (size_t)pass * a.ntiles * bins + b;
+                uint64_t excl = 0;
+                if (tile > 0) {
+                    if (a.lb64) {
+                        excl = lookback_pair<uint64_t>((const uint64_t*)a.lookback + slot0, bins, tile, a.status);
+                        if ((tid & 1) == 0)
+                            st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
+                                       FP64 | (excl + s_tcnt[b]));
+                    } else {
+                        excl = lookback_pair<uint32_t>((const uint32_t*)a.lookback + slot0, bins, tile, a.status);
+                        if ((tid & 1) == 0)
+                            st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
+                                       FP32 | (uint32_t)(excl + s_tcnt[b]));
+                    }
+                }
+                if ((tid & 1) == 0) s_gbase[b] = boff[b] + excl - s_excl[b];
+            }
+        } else {
             const unsigned long long* boff = a.counts + (size_t)pass * bins;
 #pragma unroll
             for (int j = 0; j < PER_MAX; ++j) {

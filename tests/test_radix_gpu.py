@@ -100,9 +100,9 @@ def test_digit_widths(evo, d, dtype):
 
 def tile_fits(block, kpt, w, pairs, d, rank):
     """Shared memory of one radix CTA: three tile buffers, per-warp digit
-    counters, digit offsets and bases, two mbarriers (<= 227 KB less 1 KB).
+    counters, digit offsets, counts and bases, two mbarriers (<= 227 KB less 1 KB).
     Rank mode 3 keeps its match masks in the reorder buffer."""
-    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * (1 << d) * 2 + (1 << d) * 12 + 16
+    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * (1 << d) * 2 + (1 << d) * 16 + 16
     return smem <= 232448 - 1024
 
 
