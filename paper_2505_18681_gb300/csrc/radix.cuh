@@ -330,78 +330,6 @@ __device__ __forceinline__ uint64_t lookback_digit(const S* slot0, size_t stride
     return excl;
 }
 
-// Decoupled look-back for one digit by a pair of adjacent lanes: the lane
-// with q = 0 reads the 16 nearest unread predecessors, q = 1 the 16 beyond, so
-// one L2 round trip covers 32 tiles.  Both lanes return the same sum.
-template <typename S>
-__device__ __forceinline__ uint64_t lookback_pair(const S* slot0, size_t stride, long long tile,
-                                                  uint32_t* status) {
-    constexpr int FB = sizeof(S) * 8 - 2;
-    const S cmask = ((S)1 << FB) - 1;
-    const int lane = threadIdx.x & 31;
-    const int q = lane & 1;
-    const unsigned pm = 3u << (lane & ~1);
-    uint64_t excl = 0;
-    long long t0 = tile - 1;
-    uint32_t polls = 0;
-    for (;;) {
-        S v[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const long long t = t0 - q * 16 - i;
-            v[i] = t >= 0 ? ld_relaxed(slot0 + (size_t)t * stride) : ((S)2 << FB);
-        }
-        uint64_t sum = 0;
-        int adv = 0;
-        bool fin = false, blk = false;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if (!fin && !blk) {
-                const uint32_t f = (uint32_t)(v[i] >> FB);
-                if (f == 0) {
-                    blk = true;
-                } else {
-                    sum += (uint64_t)(v[i] & cmask);
-                    ++adv;
-                    if (f == 2) fin = true;
-                }
-            }
-        }
-        const int st = adv | (fin ? 64 : 0) | (blk ? 128 : 0);
-        const uint64_t sum0 = __shfl_sync(pm, sum, lane & ~1);
-        const uint64_t sum1 = __shfl_sync(pm, sum, lane | 1);
-        const int st0 = __shfl_sync(pm, st, lane & ~1);
-        const int st1 = __shfl_sync(pm, st, lane | 1);
-        bool waiting = false;
-        if (st0 & 64) {                    // inclusive prefix among the near 16
-            excl += sum0;
-            break;
-        } else if (st0 & 128) {            // near window blocked on an unpublished tile
-            excl += sum0;
-            t0 -= st0 & 63;
-            waiting = true;
-        } else {                           // near 16 were aggregates: go on with the far 16
-            excl += sum0 + sum1;
-            if (st1 & 64) break;
-            if (st1 & 128) {
-                t0 -= 16 + (st1 & 63);
-                waiting = true;
-            } else {
-                t0 -= 32;
-            }
-        }
-        if (waiting) {
-            if (++polls > kSpinLimit) {
-                atomicOr(status, ST_TIMEOUT);
-                break;
-            }
-            if ((polls & 255u) == 0 && ld_relaxed(status) != 0) break;
-            __nanosleep(32);
-        }
-    }
-    return excl;
-}
-
 // CTAs per SM the register budget is tuned for: about 40 registers plus one
 // per key of the thread.
 constexpr int onesweep_min_blocks(int block, int kpt) {
@@ -597,30 +525,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         // ---- decoupled look-back for the owned digits.  No barrier follows:
         // threads without digits to resolve go straight on to the reorder,
         // which overlaps the look-back's L2 round trips.
-        if (2 * bins <= BLOCK) {
-            // two lanes per digit, warps [0, 2 * bins / 32); the other warps
-            // start the reorder at once
-            if (tid < 2 * bins) {
-                const int b = tid >> 1;
-                const unsigned long long* boff = a.counts + (size_t)pass * bins;
-                const size_t slot0 = (size_t)pass * a.ntiles * bins + b;
-                uint64_t excl = 0;
-                if (tile > 0) {
-                    if (a.lb64) {
-                        excl = lookback_pair<uint64_t>((const uint64_t*)a.lookback + slot0, bins, tile, a.status);
-                        if ((tid & 1) == 0)
-                            st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
-                                       FP64 | (excl + s_tcnt[b]));
-                    } else {
-                        excl = lookback_pair<uint32_t>((const uint32_t*)a.lookback + slot0, bins, tile, a.status);
-                        if ((tid & 1) == 0)
-                            st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
-                                       FP32 | (uint32_t)(excl + s_tcnt[b]));
-                    }
-                }
-                if ((tid & 1) == 0) s_gbase[b] = boff[b] + excl - s_excl[b];
-            }
-        } else {
+        {
             const unsigned long long* boff = a.counts + (size_t)pass * bins;
 #pragma unroll
             for (int j = 0; j < PER_MAX; ++j) {
