@@ -469,90 +469,31 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         }
         __syncthreads();
 
-        // ---- tile digit counts; per digit, the exclusive prefix over warps
-        // of the warp counts, biased by the digit's offset in the tile (so the
-        // reorder needs one lookup per key); publish each digit's tile
-        // aggregate (tile 0: its inclusive prefix)
+        // ---- tile digit counts; warp counts -> exclusive prefix over warps
         constexpr int per = PER_MAX;
         const int b0 = tid * per;
         uint32_t cnt[PER_MAX];
         uint32_t mysum = 0;
-        constexpr int G = (BLOCK >= 2 * bins) ? ((BLOCK / bins) < 4 ? (BLOCK / bins) : 4) : 1;
-        if (G > 1) {
-            // G adjacent threads per digit, each over WARPS / G warps
-            constexpr int WPG = WARPS / G;
-            const int b = tid / G, g = tid % G;
-            uint32_t loc = 0;
-            if (b < bins) {
 #pragma unroll
-                for (int w = 0; w < WPG; ++w) loc += s_whist[(g * WPG + w) * bins + b];
-            }
-            uint32_t inc = loc;   // inclusive prefix over the digit's G threads
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o, G);
-                if (g >= o) inc += y;
-            }
-            const uint32_t tot = __shfl_sync(0xffffffffu, inc, G - 1, G);
-            cnt[0] = tot;
-            mysum = (g == 0 && b < bins) ? tot : 0u;
-            if (g == 0 && b < bins) {
-                s_tcnt[b] = tot;
+        for (int j = 0; j < PER_MAX; ++j) {
+            cnt[j] = 0;
+            const int b = b0 + j;
+            if (j < per && b < bins) {
+                uint32_t s = 0;
+#pragma unroll 4
+                for (int w = 0; w < WARPS; ++w) {
+                    const uint32_t c = s_whist[w * bins + b];
+                    s_whist[w * bins + b] = (uint16_t)s;
+                    s += c;
+                }
+                cnt[j] = s;
+                mysum += s;
+                s_tcnt[b] = s;
                 const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
                 if (a.lb64)
-                    st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | tot);
+                    st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | s);
                 else
-                    st_relaxed((uint32_t*)a.lookback + slot, (tile == 0 ? FP32 : FA32) | tot);
-            }
-            uint32_t tex;
-            const uint32_t ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tex);
-            const uint32_t dbase = __shfl_sync(0xffffffffu, ex, 0, G);   // digit offset in the tile
-            if (b < bins) {
-                if (g == 0) s_excl[b] = dbase;
-                uint32_t run = dbase + inc - loc;
-#pragma unroll
-                for (int w = 0; w < WPG; ++w) {
-                    const int i = (g * WPG + w) * bins + b;
-                    const uint32_t c = s_whist[i];
-                    s_whist[i] = (uint16_t)run;
-                    run += c;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < PER_MAX; ++j) {
-                cnt[j] = 0;
-                const int b = b0 + j;
-                if (j < per && b < bins) {
-                    uint32_t s = 0;
-#pragma unroll 4
-                    for (int w = 0; w < WARPS; ++w) s += s_whist[w * bins + b];
-                    cnt[j] = s;
-                    mysum += s;
-                    s_tcnt[b] = s;
-                    const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
-                    if (a.lb64)
-                        st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | s);
-                    else
-                        st_relaxed((uint32_t*)a.lookback + slot, (tile == 0 ? FP32 : FA32) | s);
-                }
-            }
-            uint32_t tot;
-            uint32_t ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tot);
-#pragma unroll
-            for (int j = 0; j < PER_MAX; ++j) {
-                const int b = b0 + j;
-                if (j < per && b < bins) {
-                    s_excl[b] = ex;
-                    uint32_t run = ex;
-#pragma unroll 4
-                    for (int w = 0; w < WARPS; ++w) {
-                        const uint32_t c = s_whist[w * bins + b];
-                        s_whist[w * bins + b] = (uint16_t)run;
-                        run += c;
-                    }
-                }
-                ex += cnt[j];
+                    st_relaxed((uint32_t*)a.lookback + slot, (tile == 0 ? FP32 : FA32) | s);
             }
         }
         // Claim the next tile only now, once this tile's aggregates are out:
@@ -568,6 +509,16 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                 mbar_arrive_expect_tx(&s_bar[cur ^ 1], (uint32_t)(KB + VB));
                 bulk_load(nb, src + (size_t)nx * TILE, (uint32_t)KB, &s_bar[cur ^ 1]);
                 if (PAIRS) bulk_load(nb + KB, vsrc + (size_t)nx * TILE, (uint32_t)VB, &s_bar[cur ^ 1]);
+            }
+        }
+        {
+            uint32_t tot;
+            uint32_t ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tot);
+#pragma unroll
+            for (int j = 0; j < PER_MAX; ++j) {
+                const int b = b0 + j;
+                if (j < per && b < bins) s_excl[b] = ex;
+                ex += cnt[j];
             }
         }
         __syncthreads();   // s_excl and the warp prefixes are complete
@@ -587,12 +538,12 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                             excl = lookback_digit<uint64_t, 16>((const uint64_t*)a.lookback + slot0, bins,
                                                                tile, a.status);
                             st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
-                                       FP64 | (excl + s_tcnt[b]));
+                                       FP64 | (excl + cnt[j]));
                         } else {
-                            excl = lookback_digit<uint32_t, 32>((const uint32_t*)a.lookback + slot0, bins,
+                            excl = lookback_digit<uint32_t, 16>((const uint32_t*)a.lookback + slot0, bins,
                                                                tile, a.status);
                             st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
-                                       FP32 | (uint32_t)(excl + s_tcnt[b]));
+                                       FP32 | (uint32_t)(excl + cnt[j]));
                         }
                     }
                     s_gbase[b] = boff[b] + excl - s_excl[b];
@@ -610,7 +561,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     U k = s_keys[s];
                     if (desc.xin) k = map_fwd(k, map);
                     const uint32_t dig = dr[i] & 0xFFFFu;
-                    const uint32_t pos = wh[dig] + (dr[i] >> 16);
+                    const uint32_t pos = s_excl[dig] + wh[dig] + (dr[i] >> 16);
                     s_rkeys[pos] = k;
                     if (PAIRS) s_rvals[pos] = s_vals[s];
                 }
