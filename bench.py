@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--kpt", type=int, default=0)
     ap.add_argument("--rank-mode", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=1 << 23, help="keys per distribution for the oracle")
+    ap.add_argument("--workload", default="nine", choices=["nine", "floatpairs", "segmented", "u32big"],
+                    help="nine: the headline workload; the others measure the other configurations")
+    ap.add_argument("--segments", type=int, default=100_000)
     return ap.parse_args()
 
 
@@ -231,6 +234,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload != "nine":
+        other_workload(args)
         return
     import torch
     import torch.distributed as tdist
@@ -444,6 +450,126 @@ def measure_e2e(evo, xs, out, params, stream, n, w, args, barrier, ws, dev):
     keys = n * len(xs) * ws
     return {"value": keys / (ms * 1e-3) / 1e9, "unit": "GKeys/s", "h2d_bytes_per_step": n * w * len(xs),
             "d2h_bytes_per_step": n * w * len(xs), "ms_per_step": ms, "steps": steps}
+
+
+# ---------------------------------------------------------------------------
+# The other configurations (one JSON line each; not the headline bench line).
+# ---------------------------------------------------------------------------
+def _time_steps(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def other_workload(args):
+    import torch
+
+    import paper_2505_18681_gb300 as evo
+    from paper_2505_18681_gb300 import inputs
+    evo.library()
+    stream = torch.cuda.current_stream()
+    peak, peak_src = measured_peaks()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    line = {"metric": METRIC, "unit": "GKeys/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "floatpairs":
+        n = 500_000_000 if args.n == 1_000_000_000 else args.n
+        x = inputs.generate("float_mix", n, torch.float64, seed=42, device="cuda")
+        v = torch.arange(n, dtype=torch.int64, device="cuda").to(torch.int32).view(torch.uint32)
+        ko, vo = torch.empty_like(x), torch.empty_like(v)
+        p = evo.make_params(algo="radix", stream=stream)
+        launches0 = evo.kernel_launches()
+        evo.profile(True)
+        sampler.start()
+        ms = _time_steps(lambda: evo.sort_pairs(x, v, ko, vo, params=p), args.steps, args.warmup, stream)
+        clocks = sampler.stop()
+        recs = [r for r in evo.profile_read() if r["kind"] == "radix_onesweep" and r["active"]]
+        evo.profile(False)
+        evo.sync()
+        ach = sum(r["bytes"] for r in recs) / 1e9 / (sum(r["ms"] for r in recs) * 1e-3) if recs else 0.0
+        line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="f64+u32",
+                    config={"workload": "stable key/value argsort, %d float64 keys (uniform [-1e6,1e6], 1%% "
+                            "duplicates, -0.0/+0.0/NaN sprinkled) with uint32 index payload" % n},
+                    roofline={"bound": "hbm", "kernel": "radix_onesweep (pairs)", "achieved": ach, "peak": peak,
+                              "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src},
+                    clocks=clocks, gpu_launches=evo.kernel_launches() - launches0)
+    elif args.workload == "u32big":
+        n = 10_000_000_000 if args.n == 1_000_000_000 else args.n
+        x = inputs.generate("uniform", n, torch.uint32, seed=42, device="cuda")
+        y = torch.empty_like(x)
+        p = evo.make_params(algo="radix", stream=stream)
+        launches0 = evo.kernel_launches()
+        evo.profile(True)
+        sampler.start()
+        ms = _time_steps(lambda: evo.sort(x, out=y, params=p), args.steps, args.warmup, stream)
+        clocks = sampler.stop()
+        recs = [r for r in evo.profile_read() if r["kind"] == "radix_onesweep" and r["active"]]
+        evo.profile(False)
+        evo.sync()
+        ach = sum(r["bytes"] for r in recs) / 1e9 / (sum(r["ms"] for r in recs) * 1e-3) if recs else 0.0
+        line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="u32",
+                    config={"workload": "%d uint32 keys uniform (%.0f GB, double-buffered in HBM), one sort"
+                            % (n, n * 4 / 1e9)},
+                    roofline={"bound": "hbm", "kernel": "radix_onesweep", "achieved": ach, "peak": peak,
+                              "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src},
+                    clocks=clocks, gpu_launches=evo.kernel_launches() - launches0)
+    else:   # segmented
+        lens = inputs.segment_lengths(args.segments, 16, 1_000_000, seed=42)
+        keys, offs = inputs.segmented_keys(lens, torch.int32, seed=42, device="cuda")
+        d_offs = offs.to("cuda")
+        total = keys.numel()
+        work = torch.empty_like(keys)
+        # tier threshold chosen by timing every allowed value (the batched path's only knob)
+        best_cap, best_ms = None, None
+        for cap in (1024, 2048, 4096, 8192):
+            p = evo.make_params(seg_block_cap=cap, stream=stream)
+
+            def run_batched(p=p):
+                work.copy_(keys)
+                evo.segmented_sort(work, d_offs, params=p)
+            t = _time_steps(run_batched, 1, 1, stream)
+            if best_ms is None or t < best_ms:
+                best_cap, best_ms = cap, t
+        p = evo.make_params(seg_block_cap=best_cap, stream=stream)
+        copy_ms = _time_steps(lambda: work.copy_(keys), args.steps, 1, stream)
+
+        def run_batched():
+            work.copy_(keys)
+            evo.segmented_sort(work, d_offs, params=p)
+        launches0 = evo.kernel_launches()
+        sampler.start()
+        ms = _time_steps(run_batched, args.steps, args.warmup, stream) - copy_ms
+        clocks = sampler.stop()
+        batched_launches = (evo.kernel_launches() - launches0) // (args.steps + args.warmup)
+        # plain path: one default sort call per array
+        bounds = offs.tolist()
+        plain_p = evo.make_params(algo="radix", stream=stream)
+
+        def run_plain():
+            work.copy_(keys)
+            for i in range(len(bounds) - 1):
+                a, b = bounds[i], bounds[i + 1]
+                if b - a > 1:
+                    evo.sort(work[a:b], params=plain_p)
+        plain_ms = _time_steps(run_plain, 1, 1, stream) - copy_ms
+        evo.sync()
+        line.update(value=total / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="i32",
+                    config={"workload": "batched segmented sort: %d int32 arrays, log-uniform lengths 16..1e6, "
+                            "%d keys total, even arrays uniform, odd nearly sorted" % (args.segments, total),
+                            "seg_block_cap": best_cap, "launches_per_batched_sort": batched_launches},
+                    plain={"value": total / (plain_ms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": plain_ms,
+                           "batched_over_plain": plain_ms / ms, "calls": len(bounds) - 1},
+                    clocks=clocks)
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

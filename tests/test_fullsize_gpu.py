@@ -1,0 +1,172 @@
+"""Parity at the full sizes of the workloads, in the configuration bench.py
+times.  Where the single-threaded oracle finishes in seconds it checks every
+element; where it does not, the output is checked by properties that fix a
+sort at any size, computed with plain PyTorch reductions (independent of the
+library's kernels): non-decreasing order, equal multisets (two independent
+hash sums), and sampled order statistics (y[i] is the i-th smallest input:
+#(x < y[i]) <= i < #(x <= y[i])); segmented output additionally has every
+segment checked against its own input, and a sample of segments against the
+oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+CHUNK = 1 << 27
+M1 = -7046029254386353131          # odd 64-bit multipliers of two mixing hashes
+M2 = -4658895280553007687
+
+
+def _mix(v, m):
+    v = v * m
+    v = v ^ ((v >> 29) & ((1 << 35) - 1))
+    return v * m
+
+
+def fingerprint(t):
+    s1 = torch.zeros((), dtype=torch.int64, device=t.device)
+    s2 = torch.zeros((), dtype=torch.int64, device=t.device)
+    for i in range(0, t.numel(), CHUNK):
+        v = t[i:i + CHUNK].to(torch.int64)
+        s1 += _mix(v, M1).sum()
+        s2 += _mix(v + 12345, M2).sum()
+    return int(s1), int(s2)
+
+
+def nondecreasing(y):
+    for i in range(0, y.numel() - 1, CHUNK):
+        a = y[i:i + CHUNK + 1].to(torch.int64)
+        if not bool((a[1:] >= a[:-1]).all()):
+            return False
+    return True
+
+
+def order_stats_ok(x, y, positions):
+    for i in positions:
+        v = int(y[i].to(torch.int64))
+        lt = le = 0
+        for j in range(0, x.numel(), CHUNK):
+            a = x[j:j + CHUNK].to(torch.int64)
+            lt += int((a < v).sum())
+            le += int((a <= v).sum())
+        if not (lt <= i < le):
+            return False
+    return True
+
+
+@pytest.fixture(scope="module")
+def evo():
+    import paper_2505_18681_gb300 as evo
+    evo.library()
+    return evo
+
+
+def test_nine_distributions_1e9_int64_tuned(evo):
+    """Config 2: 1e9 int64 keys under nine distributions, tuned parameters
+    chosen by the dispatcher, as bench.py runs them."""
+    import os
+    from paper_2505_18681_gb300 import inputs
+    table = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2505_18681_gb300",
+                         "tuned", "gb300_int64.txt")
+    evo.table_clear()
+    evo.table_load(table)
+    n = 1_000_000_000
+    y = torch.empty(n, dtype=torch.int64, device="cuda")
+    try:
+        for dist in ("uniform", "gaussian", "sorted", "reverse", "nearly_sorted", "distinct16", "zipf", "equal",
+                     "uniform1000"):
+            x = inputs.generate(dist, n, torch.int64, seed=42, device="cuda")
+            pd, _ = evo.plan(x)
+            evo.sort(x, out=y, **pd)
+            evo.sync()
+            assert nondecreasing(y), dist
+            assert fingerprint(x) == fingerprint(y), dist
+            assert order_stats_ok(x, y, [0, 123_456_789, 500_000_000, n - 1]), dist
+            del x
+    finally:
+        evo.table_clear()
+
+
+def test_float64_pairs_5e8_full_oracle(evo):
+    """Config 3: 5e8 float64 keys with uint32 index payload; every key bit and
+    every value compared with the oracle's stable argsort."""
+    from paper_2505_18681_gb300 import inputs
+    n = 500_000_000
+    x = inputs.generate("float_mix", n, torch.float64, seed=42, device="cuda")
+    v = torch.arange(n, dtype=torch.int64, device="cuda").to(torch.int32).view(torch.uint32)
+    ko, vo = torch.empty_like(x), torch.empty_like(v)
+    evo.sort_pairs(x, v, ko, vo, algo="radix")
+    evo.sync()
+    ek, ev = oracle.radix_sort(x.cpu().numpy(), v.cpu().numpy())
+    assert np.array_equal(ko.cpu().numpy().view(np.uint64), ek.view(np.uint64))
+    assert np.array_equal(vo.cpu().numpy(), ev)
+
+
+def test_uint32_1e10(evo):
+    """Config 5: 1e10 uint32 keys (40 GB) sorted once, double-buffered in HBM."""
+    from paper_2505_18681_gb300 import inputs
+    n = 10_000_000_000
+    x = inputs.generate("uniform", n, torch.uint32, seed=42, device="cuda")
+    y = torch.empty_like(x)
+    evo.sort(x, out=y, algo="radix")
+    evo.sync()
+    assert nondecreasing_u32(y)
+    assert fingerprint(x.view(torch.int32)) == fingerprint(y.view(torch.int32))
+    assert order_stats_u32(x, y, [0, 4_321_000_000, n - 1])
+
+
+def nondecreasing_u32(y):
+    for i in range(0, y.numel() - 1, CHUNK):
+        a = y[i:i + CHUNK + 1].view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        if not bool((a[1:] >= a[:-1]).all()):
+            return False
+    return True
+
+
+def order_stats_u32(x, y, positions):
+    for i in positions:
+        v = int(y[i:i + 1].view(torch.int32).to(torch.int64)) & 0xFFFFFFFF
+        lt = le = 0
+        for j in range(0, x.numel(), CHUNK):
+            a = x[j:j + CHUNK].view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+            lt += int((a < v).sum())
+            le += int((a <= v).sum())
+        if not (lt <= i < le):
+            return False
+    return True
+
+
+def test_segmented_100k_arrays(evo):
+    """Config 4: 100,000 int32 arrays, log-uniform lengths 16..1e6 (about 9e9
+    keys), one batched segmented sort; every segment checked for order and
+    multiset, 300 sampled segments against the oracle."""
+    from paper_2505_18681_gb300 import inputs
+    lens = inputs.segment_lengths(100_000, 16, 1_000_000, seed=42)
+    keys, offs = inputs.segmented_keys(lens, torch.int32, seed=42, device="cuda")
+    d_offs = offs.to("cuda")
+    y = keys.clone()
+    evo.segmented_sort(y, d_offs)
+    evo.sync()
+    total = keys.numel()
+    starts = torch.zeros(total + 1, dtype=torch.bool, device="cuda")
+    starts[d_offs] = True
+    nseg = lens.numel()
+    ok = True
+    fx = torch.zeros(nseg, dtype=torch.int64, device="cuda")
+    fy = torch.zeros(nseg, dtype=torch.int64, device="cuda")
+    for i in range(0, total, CHUNK):
+        j = min(total, i + CHUNK)
+        a = y[i:min(total, j + 1)].to(torch.int64)
+        ok &= bool(((a[1:] >= a[:-1]) | starts[i + 1:i + a.numel()]).all())
+        seg = torch.searchsorted(d_offs, torch.arange(i, j, device="cuda"), right=True) - 1
+        fx.index_add_(0, seg, _mix(keys[i:j].to(torch.int64), M1))
+        fy.index_add_(0, seg, _mix(y[i:j].to(torch.int64), M1))
+    assert ok, "a segment is out of order"
+    assert torch.equal(fx, fy), "a segment's multiset changed"
+    rng = np.random.default_rng(1)
+    for s in rng.choice(nseg, 300, replace=False):
+        a, b = int(offs[s]), int(offs[s + 1])
+        assert np.array_equal(y[a:b].cpu().numpy(), oracle.radix_sort(keys[a:b].cpu().numpy()))
