@@ -342,9 +342,11 @@ int segmented_sort(void* keys, size_t total, const uint64_t* off, size_t nseg, i
             const int wi = w == 4 ? 0 : 1;
             auto kern = w == 4 ? (void (*)(SegArgs))seg_sort<uint32_t> : (void (*)(SegArgs))seg_sort<uint64_t>;
             if (resident[wi] == 0) {
-                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                // sized for the largest block tier allowed, so every seg_block_cap fits
+                const size_t smax = seg_smem_bytes(w, w == 4 ? 8192 : 4096);
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
                 int nb = 0;
-                if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kSB, smem);
+                if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kSB, smax);
                 resident[wi] = nb > 0 ? nb : 1;
             }
             if (e == cudaSuccess) {

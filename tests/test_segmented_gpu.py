@@ -72,6 +72,12 @@ def test_block_cap_param(evo, cap):
     run(evo, [100, 300, 1500, 5000, 9000, 70_000], torch.int64, seg_block_cap=cap)
 
 
+def test_block_cap_sequence_in_one_process(evo):
+    """Tier thresholds may change from call to call (largest last)."""
+    for cap in (256, 2048, 8192):
+        run(evo, [100, 3000, 7000, 9000, 40_000], torch.int32, seg_block_cap=cap)
+
+
 def test_low_entropy_segments(evo):
     """Large segments whose digits are mostly constant (pass skipping inside a
     segment, including odd numbers of active passes)."""
