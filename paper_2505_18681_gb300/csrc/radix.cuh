@@ -275,12 +275,16 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t dig) {
 }
 
 // Dynamic shared memory of one onesweep CTA: three tile buffers (two TMA
-// input buffers, one reorder buffer), per-warp digit counters, the tile's
-// digit offsets, counts and global bases, two mbarriers.  (Rank mode 3 keeps its
+// input buffers, one reorder buffer), per-virtual-warp digit counters, the
+// tile's digit offsets, counts, partial sums and global bases, two mbarriers.  (Rank mode 3 keeps its
 // per-warp match masks in the reorder buffer.)
+// Each warp ranks its keys as kVW independent "virtual warps" (the first and
+// second half of its keys), interleaved for instruction-level parallelism.
+constexpr int kVW = 2;
+
 __host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d, int rank) {
-    return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * ((size_t)1 << d) * 2 +
-           ((size_t)1 << d) * 16 + 16;
+    return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * kVW * ((size_t)1 << d) * 2 +
+           ((size_t)1 << d) * 32 + 16;
 }
 // Largest dynamic shared memory a CTA may use on sm_100-class GPUs (227 KB),
 // less room for the kernel's static shared variables.
@@ -356,12 +360,14 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     unsigned char* bufs = smem;   // two input tile buffers of KB + VB bytes
     U* s_rkeys = (U*)(smem + 2 * (KB + VB));                  // reorder buffer
     uint32_t* s_rvals = (uint32_t*)(smem + 2 * (KB + VB) + KB);
+    constexpr int NVW = WARPS * kVW;   // virtual warps, in input order
     uint16_t* s_whist = (uint16_t*)(smem + 3 * (KB + VB));
-    uint32_t* s_excl = (uint32_t*)(s_whist + WARPS * bins);
+    uint32_t* s_excl = (uint32_t*)(s_whist + NVW * bins);
     uint32_t* s_tcnt = s_excl + bins;
-    unsigned long long* s_gbase = (unsigned long long*)(s_tcnt + bins);
+    uint32_t* s_part = s_tcnt + bins;   // 4 x bins partial sums
+    unsigned long long* s_gbase = (unsigned long long*)(s_part + 4 * bins);
     uint64_t* s_bar = (uint64_t*)(s_gbase + bins);
-    // RANK 3 match masks (WARPS x bins words) live in the reorder buffer,
+    // RANK 3 match masks (NVW x bins words) live in the reorder buffer,
     // which is idle while a tile is ranked
     uint32_t* s_match = (uint32_t*)s_rkeys;
     __shared__ uint32_t s_tile[2];
@@ -402,11 +408,11 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         unsigned char* kb = bufs + cur * (KB + VB);
         U* s_keys = (U*)kb;
         uint32_t* s_vals = (uint32_t*)(kb + KB);
-        uint16_t* wh = s_whist + warp * bins;
-        uint32_t* wm = s_match + warp * bins;
-        for (int i = lane; i < bins / 2; i += 32) ((uint32_t*)wh)[i] = 0;
+        uint16_t* wh = s_whist + warp * kVW * bins;   // kVW rows, one per virtual warp
+        uint32_t* wm = s_match + warp * kVW * bins;
+        for (int i = lane; i < kVW * bins / 2; i += 32) ((uint32_t*)wh)[i] = 0;
         if (RANK == 3)
-            for (int i = lane; i < bins; i += 32) wm[i] = 0u;
+            for (int i = lane; i < kVW * bins; i += 32) wm[i] = 0u;
 
         // ---- keys of the tile, warp-striped (warp w owns a contiguous run of
         // 32*KPT keys; key i of a lane sits at w*32*KPT + 32*i + lane).  The
@@ -440,60 +446,96 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         }
         __syncwarp();
 
-        // ---- stable rank of each key among the equal digits of its warp
+        // ---- stable rank of each key among the equal digits of its virtual
+        // warp: keys [0, KPT/2) of a lane belong to the warp's first virtual
+        // warp, [KPT/2, KPT) to its second; the two chains are independent
         const uint32_t lt = lanemask_lt();
+        constexpr int H = KPT / kVW;
+        uint16_t* wh1 = wh + bins;
+        uint32_t* wm1 = wm + bins;
 #pragma unroll
-        for (int i = 0; i < KPT; ++i) {
-            const uint32_t dig = dr[i];
-            uint32_t peers;
+        for (int i = 0; i < H; ++i) {
+            const uint32_t d0 = dr[i], d1 = dr[i + H];
+            uint32_t p0, p1;
             if (RANK == 3) {
-                // peers from per-warp shared match masks: every lane ORs its bit
-                // into its digit's word and reads the word back
-                atomicOr(&wm[dig], 1u << lane);
+                // peers from shared match masks: every lane ORs its bit into
+                // its digit's word and reads the word back
+                atomicOr(&wm[d0], 1u << lane);
+                atomicOr(&wm1[d1], 1u << lane);
                 __syncwarp();
-                peers = wm[dig];
+                p0 = wm[d0];
+                p1 = wm1[d1];
                 __syncwarp();
             } else {
-                peers = warp_peers<RANK, D>(dig);
+                p0 = warp_peers<RANK, D>(d0);
+                p1 = warp_peers<RANK, D>(d1);
             }
-            const int leader = 31 - __clz(peers);
-            uint32_t old = 0;
-            if (lane == leader) {
-                old = wh[dig];
-                wh[dig] = (uint16_t)(old + __popc(peers));
-                if (RANK == 3) wm[dig] = 0u;
+            const int l0 = 31 - __clz(p0), l1 = 31 - __clz(p1);
+            uint32_t o0 = 0, o1 = 0;
+            if (lane == l0) {
+                o0 = wh[d0];
+                wh[d0] = (uint16_t)(o0 + __popc(p0));
+                if (RANK == 3) wm[d0] = 0u;
             }
-            old = __shfl_sync(0xffffffffu, old, leader);
-            dr[i] = dig | ((old + __popc(peers & lt)) << 16);
+            if (lane == l1) {
+                o1 = wh1[d1];
+                wh1[d1] = (uint16_t)(o1 + __popc(p1));
+                if (RANK == 3) wm1[d1] = 0u;
+            }
+            o0 = __shfl_sync(0xffffffffu, o0, l0);
+            o1 = __shfl_sync(0xffffffffu, o1, l1);
+            dr[i] = d0 | ((o0 + __popc(p0 & lt)) << 16);
+            dr[i + H] = d1 | ((o1 + __popc(p1 & lt)) << 16);
             __syncwarp();
         }
         __syncthreads();
 
-        // ---- tile digit counts; warp counts -> exclusive prefix over warps
+        // ---- tile digit counts; virtual-warp counts -> exclusive prefix over
+        // virtual warps (in input order); publish each digit's tile aggregate
+        // (tile 0: its inclusive prefix)
         constexpr int per = PER_MAX;
         const int b0 = tid * per;
-        uint32_t cnt[PER_MAX];
         uint32_t mysum = 0;
+        constexpr int G = (BLOCK >= 2 * bins) ? ((BLOCK / bins) < 4 ? (BLOCK / bins) : 4) : 1;
+        constexpr int VPG = NVW / G;   // virtual warps per group
+        if (G > 1) {
+            // thread (g, b) = tid (g-major, so a warp reads consecutive digits)
+            const int g = tid / bins, b = tid % bins;
+            if (g < G) {
+                uint32_t sum = 0;
+#pragma unroll 8
+                for (int v = 0; v < VPG; ++v) sum += s_whist[(g * VPG + v) * bins + b];
+                s_part[g * bins + b] = sum;
+            }
+            __syncthreads();
+            if (tid < bins) {
+                uint32_t t = 0;
 #pragma unroll
-        for (int j = 0; j < PER_MAX; ++j) {
-            cnt[j] = 0;
-            const int b = b0 + j;
-            if (j < per && b < bins) {
-                uint32_t s = 0;
-#pragma unroll 4
-                for (int w = 0; w < WARPS; ++w) {
-                    const uint32_t c = s_whist[w * bins + b];
-                    s_whist[w * bins + b] = (uint16_t)s;
-                    s += c;
-                }
-                cnt[j] = s;
-                mysum += s;
-                s_tcnt[b] = s;
-                const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
+                for (int q = 0; q < G; ++q) t += s_part[q * bins + tid];
+                mysum = t;
+                s_tcnt[tid] = t;
+                const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + tid;
                 if (a.lb64)
-                    st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | s);
+                    st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | t);
                 else
-                    st_relaxed((uint32_t*)a.lookback + slot, (tile == 0 ? FP32 : FA32) | s);
+                    st_relaxed((uint32_t*)a.lookback + slot, (tile == 0 ? FP32 : FA32) | t);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < PER_MAX; ++j) {
+                const int b = b0 + j;
+                if (j < per && b < bins) {
+                    uint32_t t = 0;
+#pragma unroll 8
+                    for (int v = 0; v < NVW; ++v) t += s_whist[v * bins + b];
+                    mysum += t;
+                    s_tcnt[b] = t;
+                    const size_t slot = ((size_t)pass * a.ntiles + tile) * bins + b;
+                    if (a.lb64)
+                        st_relaxed((uint64_t*)a.lookback + slot, (tile == 0 ? FP64 : FA64) | t);
+                    else
+                        st_relaxed((uint32_t*)a.lookback + slot, (tile == 0 ? FP32 : FA32) | t);
+                }
             }
         }
         // Claim the next tile only now, once this tile's aggregates are out:
@@ -514,11 +556,36 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         {
             uint32_t tot;
             uint32_t ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tot);
+            if (G > 1) {
+                if (tid < bins) s_excl[tid] = ex;
+                const int g = tid / bins, b = tid % bins;
+                if (g < G) {
+                    uint32_t run = 0;
+                    for (int q = 0; q < g; ++q) run += s_part[q * bins + b];
+#pragma unroll 8
+                    for (int v = 0; v < VPG; ++v) {
+                        const int i = (g * VPG + v) * bins + b;
+                        const uint32_t c = s_whist[i];
+                        s_whist[i] = (uint16_t)run;
+                        run += c;
+                    }
+                }
+            } else {
 #pragma unroll
-            for (int j = 0; j < PER_MAX; ++j) {
-                const int b = b0 + j;
-                if (j < per && b < bins) s_excl[b] = ex;
-                ex += cnt[j];
+                for (int j = 0; j < PER_MAX; ++j) {
+                    const int b = b0 + j;
+                    if (j < per && b < bins) {
+                        s_excl[b] = ex;
+                        ex += s_tcnt[b];
+                        uint32_t run = 0;
+#pragma unroll 8
+                        for (int v = 0; v < NVW; ++v) {
+                            const uint32_t c = s_whist[v * bins + b];
+                            s_whist[v * bins + b] = (uint16_t)run;
+                            run += c;
+                        }
+                    }
+                }
             }
         }
         __syncthreads();   // s_excl and the warp prefixes are complete
@@ -538,12 +605,12 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                             excl = lookback_digit<uint64_t, 16>((const uint64_t*)a.lookback + slot0, bins,
                                                                tile, a.status);
                             st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
-                                       FP64 | (excl + cnt[j]));
+                                       FP64 | (excl + s_tcnt[b]));
                         } else {
                             excl = lookback_digit<uint32_t, 16>((const uint32_t*)a.lookback + slot0, bins,
                                                                tile, a.status);
                             st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
-                                       FP32 | (uint32_t)(excl + cnt[j]));
+                                       FP32 | (uint32_t)(excl + s_tcnt[b]));
                         }
                     }
                     s_gbase[b] = boff[b] + excl - s_excl[b];
@@ -561,7 +628,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     U k = s_keys[s];
                     if (desc.xin) k = map_fwd(k, map);
                     const uint32_t dig = dr[i] & 0xFFFFu;
-                    const uint32_t pos = s_excl[dig] + wh[dig] + (dr[i] >> 16);
+                    const uint32_t pos = s_excl[dig] + (i < H ? wh : wh1)[dig] + (dr[i] >> 16);
                     s_rkeys[pos] = k;
                     if (PAIRS) s_rvals[pos] = s_vals[s];
                 }
@@ -607,6 +674,6 @@ __global__ void __launch_bounds__(256) radix_fixup(RadixArgs a) {
 namespace evosort {
 // The rank-3 match masks must fit in the reorder buffer.
 constexpr bool match_masks_fit(int block, int kpt, int w, int d) {
-    return (size_t)(block / 32) * ((size_t)1 << d) * 4 <= (size_t)block * kpt * w;
+    return (size_t)(block / 32) * kVW * ((size_t)1 << d) * 4 <= (size_t)block * kpt * w;
 }
 }  // namespace evosort

@@ -100,9 +100,10 @@ def test_digit_widths(evo, d, dtype):
 
 def tile_fits(block, kpt, w, pairs, d, rank):
     """Shared memory of one radix CTA: three tile buffers, per-warp digit
-    counters, digit offsets, counts and bases, two mbarriers (<= 227 KB less 1 KB).
+    counters (two virtual warps per warp), digit offsets, counts, partial sums
+    and bases, two mbarriers (<= 227 KB less 1 KB).
     Rank mode 3 keeps its match masks in the reorder buffer."""
-    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * (1 << d) * 2 + (1 << d) * 16 + 16
+    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * 2 * (1 << d) * 2 + (1 << d) * 32 + 16
     return smem <= 232448 - 1024
 
 
@@ -121,7 +122,8 @@ def test_tile_shapes_and_ranking(evo, shape, rank, d):
         for pairs in (False, True):
             runner = run_pairs if pairs else run_keys
             compiled = rank == 2 or (rank == 1 and d == 8) or (rank == 3 and d <= 8)
-            if compiled and tile_fits(block, kpt, w, pairs, d, rank):
+            masks_fit = rank != 3 or block // 32 * 2 * (1 << d) * 4 <= block * kpt * w
+            if compiled and masks_fit and tile_fits(block, kpt, w, pairs, d, rank):
                 runner(evo, x, **kw)
             else:
                 with pytest.raises(evo.EvoSortError) as ei:
