@@ -272,10 +272,10 @@ static void defaults_for(int w, Plan* pl) {
 // Default radix tile shape: the first of a preference list (largest tiles
 // first, so fewer tiles are in flight in the look-back) that fits.
 static void default_tile_shape(int w, bool pairs, Plan* pl) {
-    static const int pref4[][2] = {{512, 32}, {1024, 16}, {512, 16}, {1024, 8}, {256, 16}};
-    static const int pref8[][2] = {{1024, 8}, {512, 16}, {256, 16}, {1024, 16}, {512, 32}};
+    static const int pref4[][2] = {{512, 32}, {1024, 16}, {512, 16}, {1024, 8}, {256, 16}, {256, 8}};
+    static const int pref8[][2] = {{1024, 8}, {512, 16}, {256, 16}, {512, 8}, {256, 8}, {256, 8}};
     const int(*pref)[2] = w == 4 ? pref4 : pref8;
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 6; ++i) {
         const int b = pl->block_size ? pl->block_size : pref[i][0];
         const int k = pl->keys_per_thread ? pl->keys_per_thread : pref[i][1];
         if (onesweep_config_fits(w, pairs, b, k, pl->digit_bits, pl->rank_mode) &&

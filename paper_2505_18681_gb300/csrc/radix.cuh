@@ -284,7 +284,7 @@ constexpr int kVW = 2;
 
 __host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d, int rank) {
     return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * kVW * ((size_t)1 << d) * 2 +
-           ((size_t)1 << d) * 32 + 16;
+           ((size_t)1 << d) * 16 + ((2 << d) <= block ? ((size_t)1 << d) * 16 : 0) + 16;
 }
 // Largest dynamic shared memory a CTA may use on sm_100-class GPUs (227 KB),
 // less room for the kernel's static shared variables.
@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     uint16_t* s_whist = (uint16_t*)(smem + 3 * (KB + VB));
     uint32_t* s_excl = (uint32_t*)(s_whist + NVW * bins);
     uint32_t* s_tcnt = s_excl + bins;
-    uint32_t* s_part = s_tcnt + bins;   // 4 x bins partial sums
-    unsigned long long* s_gbase = (unsigned long long*)(s_part + 4 * bins);
+    uint32_t* s_part = s_tcnt + bins;   // 4 x bins partial sums (only when 2 * bins <= BLOCK)
+    unsigned long long* s_gbase = (unsigned long long*)(s_part + (2 * bins <= BLOCK ? 4 * bins : 0));
     uint64_t* s_bar = (uint64_t*)(s_gbase + bins);
     // RANK 3 match masks (NVW x bins words) live in the reorder buffer,
     // which is idle while a tile is ranked

@@ -8,6 +8,7 @@ namespace evosort {
 
 // (threads per CTA, keys per thread) pairs compiled into the library.
 #define EVOSORT_TILE_SHAPES(X) \
+    X(256, 8)                  \
     X(256, 16)                 \
     X(512, 8)                  \
     X(512, 16)                 \

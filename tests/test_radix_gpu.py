@@ -103,11 +103,13 @@ def tile_fits(block, kpt, w, pairs, d, rank):
     counters (two virtual warps per warp), digit offsets, counts, partial sums
     and bases, two mbarriers (<= 227 KB less 1 KB).
     Rank mode 3 keeps its match masks in the reorder buffer."""
-    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * 2 * (1 << d) * 2 + (1 << d) * 32 + 16
+    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * 2 * (1 << d) * 2 + (1 << d) * 16 + 16
+    if (2 << d) <= block:
+        smem += (1 << d) * 16
     return smem <= 232448 - 1024
 
 
-@pytest.mark.parametrize("shape", [(256, 16), (512, 8), (512, 16), (512, 32), (1024, 8), (1024, 16)])
+@pytest.mark.parametrize("shape", [(256, 8), (256, 16), (512, 8), (512, 16), (512, 32), (1024, 8), (1024, 16)])
 @pytest.mark.parametrize("rank", [1, 2, 3])
 @pytest.mark.parametrize("d", [6, 8, 11])
 def test_tile_shapes_and_ranking(evo, shape, rank, d):
