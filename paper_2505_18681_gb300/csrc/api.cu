@@ -279,7 +279,7 @@ static void default_tile_shape(int w, bool pairs, Plan* pl) {
         const int b = pl->block_size ? pl->block_size : pref[i][0];
         const int k = pl->keys_per_thread ? pl->keys_per_thread : pref[i][1];
         if (onesweep_config_fits(w, pairs, b, k, pl->digit_bits, pl->rank_mode) &&
-            onesweep_rank_fits(pl->rank_mode, b, k, w, pl->digit_bits)) {
+            onesweep_rank_fits(pl->rank_mode, b, k, w, pairs, pl->digit_bits)) {
             pl->block_size = b;
             pl->keys_per_thread = k;
             return;
@@ -395,7 +395,7 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     if (rc) return finish(rc, err);
     if (pl.algo == EVOSORT_ALGO_RADIX &&
         (!onesweep_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits, pl.rank_mode) ||
-         !onesweep_rank_fits(pl.rank_mode, pl.block_size, pl.keys_per_thread, w, pl.digit_bits)))
+         !onesweep_rank_fits(pl.rank_mode, pl.block_size, pl.keys_per_thread, w, pairs, pl.digit_bits)))
         return finish(EVOSORT_ERR_INVALID, "radix tile does not fit in shared memory (block_size x "
                                            "keys_per_thread too large for this key width and digit width)");
     cudaStream_t s = p ? (cudaStream_t)p->stream : nullptr;

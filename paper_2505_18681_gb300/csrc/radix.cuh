@@ -278,17 +278,24 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t dig) {
 // input buffers, one reorder buffer), per-virtual-warp digit counters, the
 // tile's digit offsets, counts, partial sums and global bases, two mbarriers.  (Rank mode 3 keeps its
 // per-warp match masks in the reorder buffer.)
-// Each warp ranks its keys as kVW independent "virtual warps" (the first and
-// second half of its keys), interleaved for instruction-level parallelism.
-constexpr int kVW = 2;
-
-__host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d, int rank) {
-    return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * kVW * ((size_t)1 << d) * 2 +
-           ((size_t)1 << d) * 16 + ((2 << d) <= block ? ((size_t)1 << d) * 16 : 0) + 16;
-}
 // Largest dynamic shared memory a CTA may use on sm_100-class GPUs (227 KB),
 // less room for the kernel's static shared variables.
 constexpr size_t kMaxDynSmem = 232448 - 1024;
+
+// Each warp ranks its keys as vw independent "virtual warps" (vw = 2: the
+// first and second half of its keys, interleaved for instruction-level
+// parallelism), each with its own digit counters.
+__host__ __device__ constexpr size_t onesweep_smem_vw(int block, int kpt, int w, bool pairs, int d, int vw) {
+    return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * vw * ((size_t)1 << d) * 2 +
+           ((size_t)1 << d) * 16 + ((2 << d) <= block ? ((size_t)1 << d) * 16 : 0) + 16;
+}
+// two virtual warps per warp where their counters fit, else one
+__host__ __device__ constexpr int onesweep_vw(int block, int kpt, int w, bool pairs, int d) {
+    return (kpt % 2 == 0 && onesweep_smem_vw(block, kpt, w, pairs, d, 2) <= kMaxDynSmem) ? 2 : 1;
+}
+__host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d, int rank) {
+    return onesweep_smem_vw(block, kpt, w, pairs, d, onesweep_vw(block, kpt, w, pairs, d));
+}
 
 // Decoupled look-back for one digit: sums the counts of the preceding tiles
 // back to the nearest inclusive prefix.  LBW slots are read per L2 round trip.
@@ -360,6 +367,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     unsigned char* bufs = smem;   // two input tile buffers of KB + VB bytes
     U* s_rkeys = (U*)(smem + 2 * (KB + VB));                  // reorder buffer
     uint32_t* s_rvals = (uint32_t*)(smem + 2 * (KB + VB) + KB);
+    constexpr int kVW = onesweep_vw(BLOCK, KPT, (int)sizeof(U), PAIRS, D);
     constexpr int NVW = WARPS * kVW;   // virtual warps, in input order
     uint16_t* s_whist = (uint16_t*)(smem + 3 * (KB + VB));
     uint32_t* s_excl = (uint32_t*)(s_whist + NVW * bins);
@@ -451,10 +459,35 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         // warp, [KPT/2, KPT) to its second; the two chains are independent
         const uint32_t lt = lanemask_lt();
         constexpr int H = KPT / kVW;
-        uint16_t* wh1 = wh + bins;
-        uint32_t* wm1 = wm + bins;
+        uint16_t* wh1 = wh + (kVW == 2 ? bins : 0);
+        uint32_t* wm1 = wm + (kVW == 2 ? bins : 0);
+        if (kVW == 1) {
 #pragma unroll
-        for (int i = 0; i < H; ++i) {
+            for (int i = 0; i < KPT; ++i) {
+                const uint32_t d0 = dr[i];
+                uint32_t p0;
+                if (RANK == 3) {
+                    atomicOr(&wm[d0], 1u << lane);
+                    __syncwarp();
+                    p0 = wm[d0];
+                    __syncwarp();
+                } else {
+                    p0 = warp_peers<RANK, D>(d0);
+                }
+                const int l0 = 31 - __clz(p0);
+                uint32_t o0 = 0;
+                if (lane == l0) {
+                    o0 = wh[d0];
+                    wh[d0] = (uint16_t)(o0 + __popc(p0));
+                    if (RANK == 3) wm[d0] = 0u;
+                }
+                o0 = __shfl_sync(0xffffffffu, o0, l0);
+                dr[i] = d0 | ((o0 + __popc(p0 & lt)) << 16);
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < (kVW == 2 ? H : 0); ++i) {
             const uint32_t d0 = dr[i], d1 = dr[i + H];
             uint32_t p0, p1;
             if (RANK == 3) {
@@ -628,7 +661,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     U k = s_keys[s];
                     if (desc.xin) k = map_fwd(k, map);
                     const uint32_t dig = dr[i] & 0xFFFFu;
-                    const uint32_t pos = s_excl[dig] + (i < H ? wh : wh1)[dig] + (dr[i] >> 16);
+                    const uint32_t pos = s_excl[dig] + ((kVW == 2 && i >= H) ? wh1 : wh)[dig] + (dr[i] >> 16);
                     s_rkeys[pos] = k;
                     if (PAIRS) s_rvals[pos] = s_vals[s];
                 }
@@ -673,7 +706,8 @@ __global__ void __launch_bounds__(256) radix_fixup(RadixArgs a) {
 
 namespace evosort {
 // The rank-3 match masks must fit in the reorder buffer.
-constexpr bool match_masks_fit(int block, int kpt, int w, int d) {
-    return (size_t)(block / 32) * kVW * ((size_t)1 << d) * 4 <= (size_t)block * kpt * w;
+constexpr bool match_masks_fit(int block, int kpt, int w, bool pairs, int d) {
+    return (size_t)(block / 32) * onesweep_vw(block, kpt, w, pairs, d) * ((size_t)1 << d) * 4 <=
+           (size_t)block * kpt * w;
 }
 }  // namespace evosort

@@ -99,8 +99,8 @@ inline bool onesweep_config_fits(int w, bool pairs, int block, int kpt, int d, i
 inline bool onesweep_rank_supported(int rank, int d) {
     return rank == 2 || (rank == 1 && d == 8) || (rank == 3 && d <= 8);
 }
-inline bool onesweep_rank_fits(int rank, int block, int kpt, int w, int d) {
-    return rank != 3 || match_masks_fit(block, kpt, w, d);
+inline bool onesweep_rank_fits(int rank, int block, int kpt, int w, bool pairs, int d) {
+    return rank != 3 || match_masks_fit(block, kpt, w, pairs, d);
 }
 
 // Defined in radix32k.cu, radix32p.cu, radix64k.cu, radix64p.cu.

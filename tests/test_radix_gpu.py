@@ -103,10 +103,22 @@ def tile_fits(block, kpt, w, pairs, d, rank):
     counters (two virtual warps per warp), digit offsets, counts, partial sums
     and bases, two mbarriers (<= 227 KB less 1 KB).
     Rank mode 3 keeps its match masks in the reorder buffer."""
-    smem = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * 2 * (1 << d) * 2 + (1 << d) * 16 + 16
+    return smem_vw(block, kpt, w, pairs, d, vw_of(block, kpt, w, pairs, d)) <= LIMIT
+
+
+LIMIT = 232448 - 1024
+
+
+def smem_vw(block, kpt, w, pairs, d, vw):
+    s = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * vw * (1 << d) * 2 + (1 << d) * 16 + 16
     if (2 << d) <= block:
-        smem += (1 << d) * 16
-    return smem <= 232448 - 1024
+        s += (1 << d) * 16
+    return s
+
+
+def vw_of(block, kpt, w, pairs, d):
+    """Two virtual warps per warp where their counters fit, else one."""
+    return 2 if kpt % 2 == 0 and smem_vw(block, kpt, w, pairs, d, 2) <= LIMIT else 1
 
 
 @pytest.mark.parametrize("shape", [(256, 8), (256, 16), (512, 8), (512, 16), (512, 32), (1024, 8), (1024, 16)])
@@ -124,7 +136,7 @@ def test_tile_shapes_and_ranking(evo, shape, rank, d):
         for pairs in (False, True):
             runner = run_pairs if pairs else run_keys
             compiled = rank == 2 or (rank == 1 and d == 8) or (rank == 3 and d <= 8)
-            masks_fit = rank != 3 or block // 32 * 2 * (1 << d) * 4 <= block * kpt * w
+            masks_fit = rank != 3 or block // 32 * vw_of(block, kpt, w, pairs, d) * (1 << d) * 4 <= block * kpt * w
             if compiled and masks_fit and tile_fits(block, kpt, w, pairs, d, rank):
                 runner(evo, x, **kw)
             else:
