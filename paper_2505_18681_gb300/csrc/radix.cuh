@@ -276,7 +276,8 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t dig) {
 
 // Dynamic shared memory of one onesweep CTA: three tile buffers (two TMA
 // input buffers, one reorder buffer), per-virtual-warp digit counters, the
-// tile's digit offsets, counts, partial sums and global bases, two mbarriers.  (Rank mode 3 keeps its
+// tile's digit offsets, counts, partial sums and global bases (64- and 32-bit),
+// two mbarriers.  (Rank mode 3 keeps its
 // per-warp match masks in the reorder buffer.)
 // Largest dynamic shared memory a CTA may use on sm_100-class GPUs (227 KB),
 // less room for the kernel's static shared variables.
@@ -287,7 +288,7 @@ constexpr size_t kMaxDynSmem = 232448 - 1024;
 // parallelism), each with its own digit counters.
 __host__ __device__ constexpr size_t onesweep_smem_vw(int block, int kpt, int w, bool pairs, int d, int vw) {
     return 3 * (size_t)block * kpt * (w + (pairs ? 4 : 0)) + (size_t)(block / 32) * vw * ((size_t)1 << d) * 2 +
-           ((size_t)1 << d) * 16 + ((2 << d) <= block ? ((size_t)1 << d) * 16 : 0) + 16;
+           ((size_t)1 << d) * 20 + ((2 << d) <= block ? ((size_t)1 << d) * 16 : 0) + 16;
 }
 // two virtual warps per warp where their counters fit, else one
 __host__ __device__ constexpr int onesweep_vw(int block, int kpt, int w, bool pairs, int d) {
@@ -374,7 +375,9 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     uint32_t* s_tcnt = s_excl + bins;
     uint32_t* s_part = s_tcnt + bins;   // 4 x bins partial sums (only when 2 * bins <= BLOCK)
     unsigned long long* s_gbase = (unsigned long long*)(s_part + (2 * bins <= BLOCK ? 4 * bins : 0));
-    uint64_t* s_bar = (uint64_t*)(s_gbase + bins);
+    uint32_t* s_gbase32 = (uint32_t*)(s_gbase + bins);   // low words, used when n < 2^32
+    const bool small_n = a.n < (1ull << 32);
+    uint64_t* s_bar = (uint64_t*)(s_gbase32 + bins);
     // RANK 3 match masks (NVW x bins words) live in the reorder buffer,
     // which is idle while a tile is ranked
     uint32_t* s_match = (uint32_t*)s_rkeys;
@@ -591,9 +594,12 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
             uint32_t ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tot);
             if (G > 1) {
                 if (tid < bins) s_excl[tid] = ex;
+                __syncthreads();
+                // prefixes biased by the digit's offset in the tile, so the
+                // reorder needs one lookup per key
                 const int g = tid / bins, b = tid % bins;
                 if (g < G) {
-                    uint32_t run = 0;
+                    uint32_t run = s_excl[b];
                     for (int q = 0; q < g; ++q) run += s_part[q * bins + b];
 #pragma unroll 8
                     for (int v = 0; v < VPG; ++v) {
@@ -609,8 +615,8 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     const int b = b0 + j;
                     if (j < per && b < bins) {
                         s_excl[b] = ex;
+                        uint32_t run = ex;
                         ex += s_tcnt[b];
-                        uint32_t run = 0;
 #pragma unroll 8
                         for (int v = 0; v < NVW; ++v) {
                             const uint32_t c = s_whist[v * bins + b];
@@ -640,13 +646,15 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                             st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
                                        FP64 | (excl + s_tcnt[b]));
                         } else {
-                            excl = lookback_digit<uint32_t, 16>((const uint32_t*)a.lookback + slot0, bins,
+                            excl = lookback_digit<uint32_t, 32>((const uint32_t*)a.lookback + slot0, bins,
                                                                tile, a.status);
                             st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
                                        FP32 | (uint32_t)(excl + s_tcnt[b]));
                         }
                     }
-                    s_gbase[b] = boff[b] + excl - s_excl[b];
+                    const unsigned long long gb = boff[b] + excl - s_excl[b];
+                    s_gbase[b] = gb;
+                    s_gbase32[b] = (uint32_t)gb;
                 }
             }
         }
@@ -661,7 +669,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     U k = s_keys[s];
                     if (desc.xin) k = map_fwd(k, map);
                     const uint32_t dig = dr[i] & 0xFFFFu;
-                    const uint32_t pos = s_excl[dig] + ((kVW == 2 && i >= H) ? wh1 : wh)[dig] + (dr[i] >> 16);
+                    const uint32_t pos = ((kVW == 2 && i >= H) ? wh1 : wh)[dig] + (dr[i] >> 16);
                     s_rkeys[pos] = k;
                     if (PAIRS) s_rvals[pos] = s_vals[s];
                 }
@@ -677,7 +685,8 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
             if (full || s < valid) {
                 const U k = s_rkeys[s];
                 const uint32_t dig = digit_of(k, shift, mask);
-                const size_t g = (size_t)(s_gbase[dig] + (unsigned long long)s);
+                const size_t g = small_n ? (size_t)(uint32_t)(s_gbase32[dig] + (uint32_t)s)
+                                         : (size_t)(s_gbase[dig] + (unsigned long long)s);
                 st_stream(dst + g, desc.xout ? map_inv(k, map) : k);
                 if (PAIRS) st_stream(vdst + g, s_rvals[s]);
             }

@@ -110,7 +110,7 @@ LIMIT = 232448 - 1024
 
 
 def smem_vw(block, kpt, w, pairs, d, vw):
-    s = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * vw * (1 << d) * 2 + (1 << d) * 16 + 16
+    s = 3 * block * kpt * (w + (4 if pairs else 0)) + block // 32 * vw * (1 << d) * 2 + (1 << d) * 20 + 16
     if (2 << d) <= block:
         s += (1 << d) * 16
     return s
