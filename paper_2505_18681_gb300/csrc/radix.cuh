@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                             st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
                                        FP64 | (excl + s_tcnt[b]));
                         } else {
-                            excl = lookback_digit<uint32_t, 32>((const uint32_t*)a.lookback + slot0, bins,
+                            excl = lookback_digit<uint32_t, 16>((const uint32_t*)a.lookback + slot0, bins,
                                                                tile, a.status);
                             st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
                                        FP32 | (uint32_t)(excl + s_tcnt[b]));
