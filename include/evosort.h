@@ -125,6 +125,30 @@ evosort_status evosort_sort_pairs_to(const void* keys_in, const uint32_t* values
                                      uint32_t* values_out, size_t n, evosort_dtype dt,
                                      const evosort_params* p);
 
+/* Sorts `count` arrays that live in HOST memory (the paper's sort of an
+ * array handed over by the caller, Algorithm 5, with the transfers to and
+ * from the GPU included).  Array i has n[i] keys of dtype dt at keys_in[i];
+ * its sorted keys go to keys_out[i] (== keys_in[i] for in place; any other
+ * overlap between an input and an output is an error).  Each array is copied
+ * to the device, sorted there by the device path with params p (AUTO and a
+ * non-empty table: the dispatcher's parameters for that array, classified
+ * from a strided sample read on the host when the call is made, so the input
+ * must already hold its keys then), and copied back.  The copies of
+ * array i+1 to the device and of array i-1 back to the host run on two
+ * internal streams while array i is sorted on p->stream, through three
+ * device slots of max(n[i]) keys allocated from the stream-ordered pool for
+ * the call.  The whole batch is ordered after earlier work on p->stream, and
+ * later work on p->stream waits for all of it: evosort_sync(p->stream) or a
+ * stream synchronisation makes the host outputs ready.  Host buffers should
+ * be page-locked (cudaHostAlloc / cudaHostRegister): pageable buffers are
+ * still sorted correctly, but the driver then stages each copy and the
+ * overlap is lost.  n[i] == 0 arrays are skipped.  Errors before anything is
+ * enqueued (bad arguments, no device memory) return a status; a failure of a
+ * later array's sort returns its status with the earlier arrays' work left
+ * enqueued. */
+evosort_status evosort_sort_host_batch(const void* const* keys_in, void* const* keys_out, const size_t* n,
+                                       size_t count, evosort_dtype dt, const evosort_params* p);
+
 /* Batched segmented sort: sorts each segment keys[offsets[i] .. offsets[i+1])
  * independently, in place, for i in [0, nseg), in one persistent launch
  * (after three small list-building kernels).  Short segments are sorted by

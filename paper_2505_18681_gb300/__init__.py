@@ -104,6 +104,9 @@ def library():
             lib.evosort_sort_pairs_to.argtypes = [vp, vp, vp, vp, sz, i, pp]
             for f in (lib.evosort_sort, lib.evosort_sort_to, lib.evosort_sort_pairs, lib.evosort_sort_pairs_to):
                 f.restype = st
+            lib.evosort_sort_host_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                    ctypes.POINTER(sz), sz, i, pp]
+            lib.evosort_sort_host_batch.restype = st
             lib.evosort_segmented_sort.argtypes = [vp, sz, vp, sz, i, pp]
             lib.evosort_segmented_sort.restype = st
             lib.evosort_segmented_workspace_bytes.argtypes = [sz, sz, i]
@@ -230,6 +233,35 @@ def sort_pairs(keys: torch.Tensor, values: torch.Tensor, keys_out: torch.Tensor 
     _check(lib.evosort_sort_pairs_to(keys.data_ptr(), values.data_ptr(), keys_out.data_ptr(),
                                      values_out.data_ptr(), keys.numel(), dt, ctypes.byref(p)))
     return keys_out, values_out
+
+
+def sort_host_batch(keys: list, out: list | None = None, *, params: Params | None = None, **kw) -> list:
+    """Sorts host (CPU) tensors of one dtype, each on its own, through the
+    device: uploads, sorts and downloads overlap across the list.  In place
+    unless ``out`` (a list of CPU tensors matching ``keys``) is given; the
+    results are ready after ``sync(stream)``.  Page-locked tensors
+    (``pin_memory()``) let the copies overlap the sorts."""
+    keys = list(keys)
+    out = keys if out is None else list(out)
+    if len(out) != len(keys):
+        raise ValueError("out must have one tensor per input")
+    if not keys:
+        return out
+    dt = _dtype_code(keys[0])
+    for a, b in zip(keys, out):
+        if a.is_cuda or b.is_cuda:
+            raise ValueError("sort_host_batch takes CPU tensors")
+        if not (a.is_contiguous() and b.is_contiguous()):
+            raise ValueError("tensors must be contiguous")
+        if a.dtype != keys[0].dtype or b.dtype != a.dtype or b.numel() != a.numel():
+            raise ValueError("all tensors must share the dtype; out must match keys in size")
+    m = len(keys)
+    ins = (ctypes.c_void_p * m)(*[a.data_ptr() for a in keys])
+    outs = (ctypes.c_void_p * m)(*[b.data_ptr() for b in out])
+    ns = (ctypes.c_size_t * m)(*[a.numel() for a in keys])
+    p = params if params is not None else make_params(**kw)
+    _check(library().evosort_sort_host_batch(ins, outs, ns, m, dt, ctypes.byref(p)))
+    return out
 
 
 def segmented_sort(keys: torch.Tensor, offsets: torch.Tensor, *, params: Params | None = None, **kw):

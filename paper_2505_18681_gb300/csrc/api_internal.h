@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "evosort.h"
+
 namespace evosort {
 
 // Resolved parameters of one sort call.
@@ -23,6 +25,10 @@ struct Plan {
 void set_error(const std::string& msg);
 void default_radix_plan(int dt, Plan* pl);
 bool table_nonempty();
+int classify_sample(const unsigned char* buf, size_t m, int dt);
+int classify_host(const void* keys, size_t n, int dt);
+bool table_lookup(int dt, size_t n, int cls, evosort_params* out);
+
 void count_launches(uint64_t k);
 int sm_count();
 uint32_t* status_word(std::string* err);

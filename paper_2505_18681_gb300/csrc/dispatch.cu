@@ -46,6 +46,75 @@ uint64_t host_map(uint64_t u, int dt) {
 
 }  // namespace
 
+// Class of a sample of m keys (raw bytes, m x key width), taken at stride
+// n / m from an array of n keys.
+int classify_sample(const unsigned char* buf, size_t m, int dt) {
+    const int w = dtype_bytes(dt);
+    std::vector<uint64_t> raw(m, 0);
+    for (size_t i = 0; i < m; ++i) {
+        uint64_t u = 0;
+        std::memcpy(&u, buf + i * w, w);
+        raw[i] = host_map(u, dt);
+    }
+    size_t asc = 0, desc = 0;
+    uint64_t vary = 0;
+    for (size_t i = 0; i + 1 < m; ++i) {
+        asc += raw[i] <= raw[i + 1];
+        desc += raw[i] >= raw[i + 1];
+    }
+    for (size_t i = 0; i < m; ++i) vary |= raw[i] ^ raw[0];
+    std::vector<uint64_t> sorted(raw);
+    std::sort(sorted.begin(), sorted.end());
+    const size_t distinct = std::unique(sorted.begin(), sorted.end()) - sorted.begin();
+    // top-byte concentration: share of the sample in the most common top byte
+    size_t top[256] = {0};
+    for (size_t i = 0; i < m; ++i) top[(raw[i] >> (8 * w - 8)) & 0xFF] += 1;
+    const size_t topmax = *std::max_element(top, top + 256);
+    int bits = 0;
+    while (bits < 64 && (vary >> bits)) ++bits;
+    if (distinct == 1) return EVOSORT_CLASS_CONSTANT;
+    if (asc >= (size_t)(0.9 * (m - 1)) && asc > desc) return EVOSORT_CLASS_SORTED;
+    if (desc >= (size_t)(0.9 * (m - 1))) return EVOSORT_CLASS_REVERSE;
+    if (distinct <= 64) return EVOSORT_CLASS_FEW;
+    if (bits <= 16) return EVOSORT_CLASS_NARROW16;
+    if (bits <= 4 * w) return EVOSORT_CLASS_NARROW;          // at most half the key bits vary
+    if (topmax * 4 > m) return EVOSORT_CLASS_SKEWED;         // a quarter in one top byte
+    return EVOSORT_CLASS_RANDOM;
+}
+
+// Class of n keys in host memory, from the same strided sample the device
+// path copies (read here directly, no CUDA call).
+int classify_host(const void* keys, size_t n, int dt) {
+    if (n < 2) return EVOSORT_CLASS_CONSTANT;
+    const int w = dtype_bytes(dt);
+    const size_t m = n < (size_t)kSample ? n : (size_t)kSample;
+    const size_t stride = n / m;
+    std::vector<unsigned char> buf(m * w);
+    for (size_t i = 0; i < m; ++i) std::memcpy(buf.data() + i * w, (const unsigned char*)keys + i * stride * w, w);
+    return classify_sample(buf.data(), m, dt);
+}
+
+// Table entry for (dt, n, cls): the class itself at the nearest size bucket,
+// else the random class; false (and *out untouched) when neither is present.
+bool table_lookup(int dt, size_t n, int cls, evosort_params* out) {
+    int bucket = 0;
+    while (bucket < 63 && (n >> (bucket + 1))) ++bucket;
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    const Entry* best = nullptr;
+    int bestd = 1 << 30;
+    for (int pass = 0; pass < 2 && !best; ++pass) {
+        const int want = pass == 0 ? cls : EVOSORT_CLASS_RANDOM;
+        for (const auto& x : g_tab)
+            if (x.dt == dt && x.cls == want && std::abs(x.bucket - bucket) < bestd) {
+                best = &x;
+                bestd = std::abs(x.bucket - bucket);
+            }
+    }
+    if (!best) return false;
+    *out = best->p;
+    return true;
+}
+
 bool table_nonempty() {
     std::lock_guard<std::mutex> lk(g_tab_mu);
     return !g_tab.empty();
@@ -70,7 +139,6 @@ evosort_status evosort_classify(const void* keys, size_t n, evosort_dtype dt, vo
     }
     const size_t m = n < (size_t)kSample ? n : (size_t)kSample;
     const size_t stride = n / m;
-    std::vector<uint64_t> raw(m, 0);
     std::vector<unsigned char> buf(m * w);
     // one strided device-to-host copy of m keys
     cudaError_t e = cudaMemcpy2DAsync(buf.data(), w, keys, stride * w, w, m, cudaMemcpyDeviceToHost,
@@ -80,37 +148,7 @@ evosort_status evosort_classify(const void* keys, size_t n, evosort_dtype dt, vo
         set_error(std::string("evosort_classify: sample copy: ") + cudaGetErrorString(e));
         return EVOSORT_ERR_CUDA;
     }
-    for (size_t i = 0; i < m; ++i) {
-        uint64_t u = 0;
-        std::memcpy(&u, buf.data() + i * w, w);
-        raw[i] = host_map(u, dt);
-    }
-    size_t asc = 0, desc = 0;
-    uint64_t vary = 0;
-    for (size_t i = 0; i + 1 < m; ++i) {
-        asc += raw[i] <= raw[i + 1];
-        desc += raw[i] >= raw[i + 1];
-    }
-    for (size_t i = 0; i < m; ++i) vary |= raw[i] ^ raw[0];
-    std::vector<uint64_t> sorted(raw);
-    std::sort(sorted.begin(), sorted.end());
-    const size_t distinct = std::unique(sorted.begin(), sorted.end()) - sorted.begin();
-    // top-byte concentration: share of the sample in the most common top byte
-    size_t top[256] = {0};
-    for (size_t i = 0; i < m; ++i) top[(raw[i] >> (8 * w - 8)) & 0xFF] += 1;
-    const size_t topmax = *std::max_element(top, top + 256);
-    int bits = 0;
-    while (bits < 64 && (vary >> bits)) ++bits;
-    int c;
-    if (distinct == 1) c = EVOSORT_CLASS_CONSTANT;
-    else if (asc >= (size_t)(0.9 * (m - 1)) && asc > desc) c = EVOSORT_CLASS_SORTED;
-    else if (desc >= (size_t)(0.9 * (m - 1))) c = EVOSORT_CLASS_REVERSE;
-    else if (distinct <= 64) c = EVOSORT_CLASS_FEW;
-    else if (bits <= 16) c = EVOSORT_CLASS_NARROW16;
-    else if (bits <= 4 * w) c = EVOSORT_CLASS_NARROW;          // at most half the key bits vary
-    else if (topmax * 4 > m) c = EVOSORT_CLASS_SKEWED;         // a quarter in one top byte
-    else c = EVOSORT_CLASS_RANDOM;
-    *cls = c;
+    *cls = classify_sample(buf.data(), m, dt);
     return EVOSORT_OK;
 }
 
@@ -200,23 +238,7 @@ evosort_status evosort_plan(const void* keys, size_t n, evosort_dtype dt, void* 
     if (table_nonempty() && n >= 2) {
         const evosort_status st = evosort_classify(keys, n, dt, stream, &cls);
         if (st != EVOSORT_OK) return st;
-        int bucket = 0;
-        while (bucket < 63 && (n >> (bucket + 1))) ++bucket;
-        std::lock_guard<std::mutex> lk(g_tab_mu);
-        const Entry* best = nullptr;
-        int bestd = 1 << 30;
-        for (int pass = 0; pass < 2 && !best; ++pass) {   // the class itself, then the random class
-            const int want = pass == 0 ? cls : EVOSORT_CLASS_RANDOM;
-            for (const auto& x : g_tab)
-                if (x.dt == dt && x.cls == want && std::abs(x.bucket - bucket) < bestd) {
-                    best = &x;
-                    bestd = std::abs(x.bucket - bucket);
-                }
-        }
-        if (best) {
-            *out = best->p;
-            out->stream = stream;
-        }
+        if (table_lookup(dt, n, cls, out)) out->stream = stream;
     }
     if (cls_out) *cls_out = cls;
     return EVOSORT_OK;

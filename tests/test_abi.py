@@ -80,6 +80,26 @@ def test_rejects_bad_arguments_without_a_gpu(lib):
     assert lib.evosort_sort(FAKE, 0, 0, bp) == 0
 
 
+def test_host_batch_rejects_bad_arguments_without_a_gpu(lib):
+    p = _params(lib)
+    bp = ctypes.byref(p)
+    VP = ctypes.c_void_p * 2
+    NS = ctypes.c_size_t * 2
+    ins, outs, ns = VP(FAKE, FAKE + 4096), VP(FAKE + 8192, FAKE + 16384), NS(10, 10)
+    f = lib.evosort_sort_host_batch
+    assert f(ins, outs, ns, 2, 9, bp) == 1                             # bad dtype
+    assert f(None, outs, ns, 2, 0, bp) == 1                            # null list
+    assert f(ins, VP(FAKE + 8, FAKE + 16384), ns, 2, 0, bp) == 1       # overlapping in/out
+    assert f(VP(FAKE + 2, FAKE + 4096), outs, ns, 2, 0, bp) == 1       # misaligned int32
+    assert f(VP(None, FAKE + 4096), outs, ns, 2, 0, bp) == 1           # null keys
+    bad = _params(lib, digit_bits=3)
+    assert f(ins, outs, ns, 2, 0, ctypes.byref(bad)) == 1              # bad parameters
+    assert b"host_batch" in lib.evosort_last_error()
+    # nothing to sort: no device work at all
+    assert f(ins, outs, ns, 0, 0, bp) == 0
+    assert f(VP(None, None), VP(None, None), NS(0, 0), 2, 0, bp) == 0
+
+
 @pytest.mark.parametrize("field,value", [("digit_bits", 3), ("digit_bits", 12), ("algo", 7),
                                          ("rank_mode", 4), ("rank_mode", -1), ("insertion_threshold", 1),
                                          ("insertion_threshold", 4096), ("block_size", 100)])
