@@ -281,7 +281,9 @@ evosort_status evosort_sort_noalloc(const void* keys_in, void* keys_out, size_t 
 
 /* Waits for params-stream work (stream = NULL: the legacy default stream) and
  * returns the first error recorded on the device since the last call
- * (EVOSORT_ERR_TIMEOUT for a bounded wait that ran out), then clears it. */
+ * (EVOSORT_ERR_TIMEOUT for a bounded wait that ran out; EVOSORT_ERR_CUDA when a
+ * radix scatter offset fell outside the array, whose stores the kernel skips;
+ * EVOSORT_ERR_INVALID for bad segment offsets), then clears it. */
 evosort_status evosort_sync(void* stream);
 
 /* Message describing the calling thread's last error ("" if none). */

@@ -527,6 +527,9 @@ evosort_status evosort_sync(void* stream) {
         uint32_t zero = 0;
         cudaMemcpy(sw, &zero, sizeof(zero), cudaMemcpyHostToDevice);
         if (v & ST_TIMEOUT) return finish(EVOSORT_ERR_TIMEOUT, "a bounded device wait ran out");
+        if (v & ST_RANGE)
+            return finish(EVOSORT_ERR_CUDA, "internal error: a radix scatter offset fell outside the array "
+                                            "(stores skipped, output invalid)");
         return finish(EVOSORT_ERR_INVALID, "device-side argument check failed (segment offsets)");
     }
     return EVOSORT_OK;

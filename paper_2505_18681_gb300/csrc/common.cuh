@@ -12,7 +12,7 @@ namespace evosort {
 enum : int { DT_I32 = 0, DT_I64 = 1, DT_U32 = 2, DT_U64 = 3, DT_F32 = 4, DT_F64 = 5 };
 
 // device status word bits (evosort_sync maps them to evosort_status)
-enum : uint32_t { ST_TIMEOUT = 1u, ST_BAD_OFFSETS = 2u };
+enum : uint32_t { ST_TIMEOUT = 1u, ST_BAD_OFFSETS = 2u, ST_RANGE = 4u };
 
 // Bounded waits: polls of a look-back slot before the kernel gives up, records
 // ST_TIMEOUT and proceeds (its output is then invalid but the context lives).

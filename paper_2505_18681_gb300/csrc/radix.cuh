@@ -687,8 +687,14 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                 const uint32_t dig = digit_of(k, shift, mask);
                 const size_t g = small_n ? (size_t)(uint32_t)(s_gbase32[dig] + (uint32_t)s)
                                          : (size_t)(s_gbase[dig] + (unsigned long long)s);
-                st_stream(dst + g, desc.xout ? map_inv(k, map) : k);
-                if (PAIRS) st_stream(vdst + g, s_rvals[s]);
+                // an offset outside the array can only come from an
+                // inconsistent look-back (a timed-out wait): record, skip
+                if (g < n) {
+                    st_stream(dst + g, desc.xout ? map_inv(k, map) : k);
+                    if (PAIRS) st_stream(vdst + g, s_rvals[s]);
+                } else {
+                    atomicOr(a.status, ST_RANGE);
+                }
             }
         }
         __syncthreads();   // the tile buffers are reused by later iterations

@@ -209,3 +209,24 @@ def test_match_mask_ranking_low_entropy(evo, dist):
         x = gen(dist, 200_003, dtype)
         run_pairs(evo, x, algo="radix", rank_mode=3, digit_bits=8)
         run_keys(evo, x, algo="radix", rank_mode=3, digit_bits=5)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "gaussian", "distinct16"])
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64], ids=str)
+def test_many_tiles_per_cta(evo, dist, dtype):
+    """Enough tiles that every persistent CTA runs many iterations and the
+    look-back walks over tiles of every state (published aggregate,
+    inclusive prefix, not yet published)."""
+    run_keys(evo, gen(dist, 12_000_017, dtype, seed=5))
+
+
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64, torch.float64], ids=str)
+def test_digit_prefix_above_2_24(evo, dtype):
+    """One digit held by 90% of 20M keys in every pass: per-digit inclusive
+    prefixes in the 32-bit look-back slots pass 2^24 (all passes stay active
+    through the other 10%)."""
+    n = 20_000_000
+    x = gen("uniform", n, dtype, seed=11)
+    pick = gen("uniform", n, torch.int64, seed=12).remainder(10) != 0
+    x = torch.where(pick, torch.full_like(x, 3), x)
+    run_keys(evo, x)
