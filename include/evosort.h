@@ -80,13 +80,19 @@ typedef struct {
     int digit_bits;           /* radix digit width d, 4..11 (default 8); the
                                  paper fixes d = 8 (one byte per pass) */
     int keys_per_thread;      /* keys each thread holds in a tile */
-    int block_size;           /* threads per CTA: 256 or 512 */
+    int block_size;           /* threads per CTA: 256, 512 or 1024 */
     int insertion_threshold;  /* mergesort base-run length T_insertion, 2..2048
                                  (default 32; Section 4.2 bounds) */
     int rank_mode;            /* radix tile ranking (how a warp finds lanes with
                                  equal digits): 1 = match.any (d = 8 only),
                                  2 = one ballot per digit bit (any d),
-                                 3 = shared-memory match masks (d <= 8; default) */
+                                 3 = shared-memory match masks (d <= 8),
+                                 4 = adaptive (d = 8; default): per pass,
+                                     match masks, or match.any when the pass's
+                                     digit is concentrated (sum of squared
+                                     digit shares > 1/32) and the pass is not
+                                     the first to run; sorts below 2^21 keys
+                                     use match masks only */
     int seg_block_cap;        /* segmented sort: segments up to this many keys are
                                  sorted by one CTA in shared memory, longer ones by
                                  a CTA-local radix sort; 256..8192 (32-bit keys),
@@ -316,6 +322,8 @@ typedef struct {
     float ms;        /* device time between the events around the launch */
     double bytes;    /* algorithmic bytes moved by the launch */
     uint64_t items;  /* keys the launch covers */
+    int rank;        /* radix pass under adaptive ranking: the ranking variant
+                        of this launch (1 or 3); 0 otherwise */
 } evosort_kernel_record;
 
 evosort_status evosort_profile(int enable);

@@ -73,7 +73,8 @@ PARAM_FIELDS = ("algo", "digit_bits", "keys_per_thread", "block_size", "insertio
 class KernelRecord(ctypes.Structure):
     """Mirror of ``evosort_kernel_record``."""
     _fields_ = [("kind", ctypes.c_int), ("pass_", ctypes.c_int), ("active", ctypes.c_int),
-                ("ms", ctypes.c_float), ("bytes", ctypes.c_double), ("items", ctypes.c_uint64)]
+                ("ms", ctypes.c_float), ("bytes", ctypes.c_double), ("items", ctypes.c_uint64),
+                ("rank", ctypes.c_int)]
 
 
 KERNEL_KINDS = {0: "radix_histogram", 1: "radix_scan", 2: "radix_onesweep", 3: "radix_fixup",
@@ -298,14 +299,16 @@ def profile(enable: bool) -> None:
 
 def profile_read() -> list:
     """Per-launch records since the last read: dicts with kind, pass, active,
-    ms (device time between the events around the launch) and bytes
-    (algorithmic traffic of the launch)."""
+    ms (device time between the events around the launch), bytes
+    (algorithmic traffic of the launch), items and rank (the ranking variant
+    of a radix pass launch under adaptive ranking, else 0)."""
     lib = library()
     cap = 1 << 16
     buf = (KernelRecord * cap)()
     n = int(lib.evosort_profile_read(buf, cap))
     return [{"kind": KERNEL_KINDS.get(r.kind, r.kind), "pass": r.pass_, "active": bool(r.active),
-             "ms": float(r.ms), "bytes": float(r.bytes), "items": int(r.items)} for r in buf[:min(n, cap)]]
+             "ms": float(r.ms), "bytes": float(r.bytes), "items": int(r.items), "rank": int(r.rank)}
+            for r in buf[:min(n, cap)]]
 
 
 def params_dict(p: Params) -> dict:

@@ -81,6 +81,7 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // ---------------------------------------------------------------------------
 struct ProfRecord {
     int kind, pass, call;
+    int rank;   // adaptive ranking: the variant this launch runs (0: not adaptive)
     double bytes;
     uint64_t items;
     cudaEvent_t e0, e1;
@@ -122,10 +123,10 @@ void prof_call_end(int call, cudaStream_t s, const PassDesc* dev_desc) {
         cudaMemcpyAsync(c.host_desc, dev_desc, sizeof(PassDesc) * c.ndesc, cudaMemcpyDeviceToHost, s);
 }
 
-ProfScope::ProfScope(int call, int kind, int pass, double bytes, uint64_t items, cudaStream_t s)
+ProfScope::ProfScope(int call, int kind, int pass, double bytes, uint64_t items, cudaStream_t s, int rank)
     : call_(call), idx_(-1), s_(s) {
     if (!g_prof_on || call < 0) return;
-    ProfRecord r{kind, pass, call, bytes, items, nullptr, nullptr};
+    ProfRecord r{kind, pass, call, rank, bytes, items, nullptr, nullptr};
     cudaEventCreate(&r.e0);
     cudaEventCreate(&r.e1);
     cudaEventRecord(r.e0, s);
@@ -205,6 +206,11 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     a.d = pl.digit_bits;
     a.npass = L.npass;
     a.lb64 = L.lb64;
+    // adaptive ranking pays one extra (empty) launch per pass; below a few
+    // million keys the match-mask ranking alone runs
+    const bool adapt = pl.rank_mode == 4 && n >= kAdaptMinKeys;
+    const int rank = pl.rank_mode == 4 ? 3 : pl.rank_mode;
+    a.adapt = adapt ? 1 : 0;
     a.ntiles = L.ntiles;
     a.desc = (PassDesc*)(base + L.off_desc);
     a.counts = (unsigned long long*)(base + L.off_counts);
@@ -231,11 +237,14 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
         if (e == cudaSuccess) e = launch_radix_aux(w, 1, 1, 0, s, a, inplace);
     }
     for (int p = 0; p < L.npass && e == cudaSuccess; ++p) {
-        ProfScope ps(call, EVOSORT_K_RADIX_ONESWEEP, p, pass_bytes, n, s);
-        if (w == 4)
-            e = launch_onesweep_u32(pairs, pl.block_size, pl.keys_per_thread, pl.rank_mode, L.ntiles, sms, s, a, p);
-        else
-            e = launch_onesweep_u64(pairs, pl.block_size, pl.keys_per_thread, pl.rank_mode, L.ntiles, sms, s, a, p);
+        for (int v = 0; v < (adapt ? 2 : 1) && e == cudaSuccess; ++v) {
+            const int r = v == 0 ? rank : 1;
+            ProfScope ps(call, EVOSORT_K_RADIX_ONESWEEP, p, pass_bytes, n, s, adapt ? r : 0);
+            if (w == 4)
+                e = launch_onesweep_u32(pairs, pl.block_size, pl.keys_per_thread, r, L.ntiles, sms, s, a, p);
+            else
+                e = launch_onesweep_u64(pairs, pl.block_size, pl.keys_per_thread, r, L.ntiles, sms, s, a, p);
+        }
     }
     size_t fix_grid = (n + 256 * 8 - 1) / (256 * 8);
     if (fix_grid > (size_t)sms * 8) fix_grid = (size_t)sms * 8;
@@ -244,7 +253,7 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
         if (e == cudaSuccess) e = launch_radix_aux(w, 2, fix_grid, 0, s, a, inplace);
     }
     prof_call_end(call, s, a.desc);
-    count_launches(3 + L.npass);
+    count_launches(3 + (adapt ? 2 : 1) * L.npass);
     if (e != cudaSuccess) {
         *err = std::string("radix launch: ") + cudaGetErrorString(e);
         return EVOSORT_ERR_CUDA;
@@ -265,7 +274,7 @@ static void defaults_for(int w, Plan* pl) {
     pl->block_size = 0;        // chosen by default_tile_shape once pairs/d are known
     pl->keys_per_thread = 0;
     pl->insertion_threshold = 32;
-    pl->rank_mode = 3;
+    pl->rank_mode = 4;
     pl->seg_block_cap = w == 4 ? 8192 : 4096;
 }
 
@@ -273,7 +282,7 @@ static void defaults_for(int w, Plan* pl) {
 // first, so fewer tiles are in flight in the look-back) that fits.
 static void default_tile_shape(int w, bool pairs, Plan* pl) {
     static const int pref4[][2] = {{512, 32}, {1024, 16}, {512, 16}, {1024, 8}, {256, 16}, {256, 8}};
-    static const int pref8[][2] = {{1024, 8}, {512, 16}, {256, 16}, {512, 8}, {256, 8}, {256, 8}};
+    static const int pref8[][2] = {{1024, 8}, {512, 16}, {512, 8}, {256, 16}, {256, 8}, {256, 8}};
     const int(*pref)[2] = w == 4 ? pref4 : pref8;
     for (int i = 0; i < 6; ++i) {
         const int b = pl->block_size ? pl->block_size : pref[i][0];
@@ -308,6 +317,7 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
     }
     if (p->rank_mode) pl->rank_mode = p->rank_mode;
     else if (pl->digit_bits > 8) pl->rank_mode = 2;   // match masks are compiled for d <= 8
+    else if (pl->digit_bits < 8) pl->rank_mode = 3;   // match.any is compiled for d = 8
     if (pl->algo != EVOSORT_ALGO_RADIX && pl->algo != EVOSORT_ALGO_MERGE) {
         *err = "params.algo must be -1, 0 or 1";
         return EVOSORT_ERR_INVALID;
@@ -316,8 +326,8 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
         *err = "params.digit_bits must be in [4, 11]";
         return EVOSORT_ERR_INVALID;
     }
-    if (pl->rank_mode < 1 || pl->rank_mode > 3) {
-        *err = "params.rank_mode must be 1, 2 or 3";
+    if (pl->rank_mode < 1 || pl->rank_mode > 4) {
+        *err = "params.rank_mode must be 1, 2, 3 or 4";
         return EVOSORT_ERR_INVALID;
     }
     if (pl->insertion_threshold < 2 || pl->insertion_threshold > 2048) {
@@ -325,7 +335,8 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
         return EVOSORT_ERR_INVALID;
     }
     if (pl->algo == EVOSORT_ALGO_RADIX && !onesweep_rank_supported(pl->rank_mode, pl->digit_bits)) {
-        *err = "params.rank_mode: 1 (match.any) needs digit_bits 8, 3 (match masks) needs digit_bits <= 8";
+        *err = "params.rank_mode: 1 (match.any) and 4 (adaptive) need digit_bits 8, 3 (match masks) needs "
+               "digit_bits <= 8";
         return EVOSORT_ERR_INVALID;
     }
     if (pl->algo == EVOSORT_ALGO_RADIX && (!pl->block_size || !pl->keys_per_thread))
@@ -563,7 +574,7 @@ size_t evosort_profile_read(evosort_kernel_record* out, size_t cap) {
         const ProfCall& c = g_prof_calls[r.call];
         if (c.host_desc) {
             if (r.kind == EVOSORT_K_RADIX_ONESWEEP && r.pass >= 0 && r.pass < c.ndesc)
-                active = c.host_desc[r.pass].active;
+                active = c.host_desc[r.pass].active && (r.rank == 0 || c.host_desc[r.pass].rank == r.rank);
             if (r.kind == EVOSORT_K_RADIX_FIXUP && r.pass >= 0 && r.pass < c.ndesc)
                 active = c.host_desc[r.pass].fixup != FIX_NONE;
         }
@@ -574,6 +585,7 @@ size_t evosort_profile_read(evosort_kernel_record* out, size_t cap) {
             out[k].ms = ms;
             out[k].bytes = active ? r.bytes : 0.0;
             out[k].items = r.items;
+            out[k].rank = r.rank;
         }
         ++k;
         cudaEventDestroy(r.e0);

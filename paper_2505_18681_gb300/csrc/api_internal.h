@@ -40,13 +40,16 @@ void prof_call_end(int call, cudaStream_t s, const PassDesc* dev_desc);
 // Records a CUDA event pair around one launch while instrumentation is on.
 class ProfScope {
   public:
-    ProfScope(int call, int kind, int pass, double bytes, uint64_t items, cudaStream_t s);
+    ProfScope(int call, int kind, int pass, double bytes, uint64_t items, cudaStream_t s, int rank = 0);
     ~ProfScope();
   private:
     int call_, idx_;
     cudaStream_t s_;
 };
 
+// Smallest sort that uses adaptive ranking (rank mode 4); smaller ones rank
+// with match masks only.
+constexpr size_t kAdaptMinKeys = (size_t)1 << 21;
 size_t radix_workspace_bytes(size_t n, int w, bool pairs, const Plan& pl);
 int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt,
                const Plan& pl, void* ws, size_t ws_bytes, cudaStream_t s, std::string* err);

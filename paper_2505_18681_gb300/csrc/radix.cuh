@@ -34,7 +34,8 @@ struct PassDesc {
     int xin;      // apply to_ordered on load (first active pass)
     int xout;     // apply from_ordered on store (last active pass)
     int fixup;    // used in the entry after the last pass
-    int pad0, pad1;
+    int rank;     // adaptive ranking: the rank mode this pass runs with
+    int pad1;
 };
 
 struct RadixArgs {
@@ -50,6 +51,7 @@ struct RadixArgs {
     int d;           // digit bits
     int npass;       // ceil(8w / d)
     int lb64;        // look-back slots are 64-bit (n >= 2^30)
+    int adapt;       // ranking chosen per pass by K2 (PassDesc::rank)
     size_t ntiles;   // tiles per pass
     PassDesc* desc;             // npass + 1 entries
     unsigned long long* counts; // npass << d digit counts, then exclusive offsets
@@ -189,9 +191,18 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
 // K2: exclusive prefix sum of each pass's digit counts, trivial-pass test and
 // the buffer chain.  One CTA of 1024 threads.
 // ---------------------------------------------------------------------------
+// Adaptive ranking (rank mode 4): the first active pass sees the keys in input
+// order and ranks with shared match masks; a later pass ranks with match.any
+// when its digit is concentrated (sum over digits of (count / n)^2 above
+// 1/32: most lanes of a warp then share a few digits, which serialises the
+// match masks' shared atomics), else with match masks.
+constexpr double kConcentrated = 1.0 / 32.0;
+
 static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int inplace) {
     __shared__ unsigned long long s_scr[33];
     __shared__ int s_trivial[64];
+    __shared__ int s_conc[64];
+    __shared__ double s_sq[32];
     const int bins = 1 << a.d;
     const int per = (bins + 1023) / 1024;   // consecutive bins per thread (<= 2)
     for (int p = 0; p < a.npass; ++p) {
@@ -199,13 +210,22 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
         unsigned long long local[2] = {0, 0};
         unsigned long long sum = 0;
         int triv = 0;
+        double sq = 0.0;
         for (int j = 0; j < per; ++j) {
             const int b = threadIdx.x * per + j;
             local[j] = b < bins ? c[b] : 0ull;
             if (local[j] == (unsigned long long)a.n) triv = 1;
             sum += local[j];
+            sq += (double)local[j] * (double)local[j];
         }
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if ((threadIdx.x & 31) == 0) s_sq[threadIdx.x >> 5] = sq;
         const int any_triv = __syncthreads_or(triv);
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 32; ++w) t += s_sq[w];
+            s_conc[p] = t > kConcentrated * (double)a.n * (double)a.n;
+        }
         unsigned long long tot;
         unsigned long long ex = block_exclusive_scan<1024>(sum, s_scr, &tot);
         for (int j = 0; j < per; ++j) {
@@ -237,6 +257,7 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
             }
             pd.xin = (k == 0);
             pd.xout = (k == e - 1);
+            pd.rank = (k > 0 && s_conc[active[k]]) ? 1 : 3;
             a.desc[active[k]] = pd;
         }
         int fix = FIX_NONE;
@@ -250,7 +271,9 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
 // K3: one onesweep pass.  RANK selects how a warp finds the lanes that share
 // a digit: 1 = match.any, 2 = one ballot per digit bit, 3 = shared-memory
 // match masks built with atomicOr (fewest instructions; serialises when many
-// lanes share a digit, as in sorted or low-entropy input).
+// lanes share a digit, as in sorted or low-entropy input).  Under adaptive
+// ranking both the RANK 1 and RANK 3 kernels are launched for every pass and
+// the one the pass descriptor does not name returns at once.
 //
 // Persistent CTAs take tiles in order from an atomic counter, so every tile's
 // predecessors are held by running CTAs and the look-back always progresses.
@@ -356,7 +379,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     constexpr size_t KB = (size_t)TILE * sizeof(U);
     constexpr size_t VB = PAIRS ? (size_t)TILE * 4 : 0;
     const PassDesc desc = a.desc[pass];
-    if (!desc.active) return;
+    if (!desc.active || (a.adapt && desc.rank != RANK)) return;
 
     constexpr int bins = 1 << D;
     const int shift = pass * D;
@@ -383,6 +406,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     uint32_t* s_match = (uint32_t*)s_rkeys;
     __shared__ uint32_t s_tile[2];
     __shared__ uint32_t s_scr[WARPS + 1];
+    __shared__ uint32_t s_bad;   // this tile's offsets left the array
 
     const size_t n = a.n;
     const U* src = sel_src<U>(a, desc.src);
@@ -416,6 +440,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         if (tile >= a.ntiles) break;
         const size_t base = (size_t)tile * TILE;
         const bool full = tile < full_tiles;
+        if (tid == 0) s_bad = 0;
         unsigned char* kb = bufs + cur * (KB + VB);
         U* s_keys = (U*)kb;
         uint32_t* s_vals = (uint32_t*)(kb + KB);
@@ -655,6 +680,17 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     const unsigned long long gb = boff[b] + excl - s_excl[b];
                     s_gbase[b] = gb;
                     s_gbase32[b] = (uint32_t)gb;
+                    // the digit's keys land in [boff + excl, boff + excl +
+                    // count): past n only after an inconsistent look-back (a
+                    // timed-out wait); the tile's stores are then skipped.
+                    // (A partial tile's padding keys count under the digit of
+                    // an all-ones key but are never stored.)
+                    const uint32_t pad = (!full && b == (int)digit_of(~(U)0, shift, mask))
+                                             ? (uint32_t)(TILE - (n - base)) : 0u;
+                    if (boff[b] + excl + (s_tcnt[b] - pad) > n) {
+                        s_bad = 1;
+                        atomicOr(a.status, ST_RANGE);
+                    }
                 }
             }
         }
@@ -678,23 +714,17 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         __syncthreads();
 
         // ---- coalesced stable scatter to the global digit buckets
-        const int valid = full ? TILE : (int)(n - base);
+        const int valid = s_bad ? 0 : (full ? TILE : (int)(n - base));
 #pragma unroll
         for (int i = 0; i < KPT; ++i) {
             const int s = i * BLOCK + tid;
-            if (full || s < valid) {
+            if ((full && valid) || s < valid) {
                 const U k = s_rkeys[s];
                 const uint32_t dig = digit_of(k, shift, mask);
                 const size_t g = small_n ? (size_t)(uint32_t)(s_gbase32[dig] + (uint32_t)s)
                                          : (size_t)(s_gbase[dig] + (unsigned long long)s);
-                // an offset outside the array can only come from an
-                // inconsistent look-back (a timed-out wait): record, skip
-                if (g < n) {
-                    st_stream(dst + g, desc.xout ? map_inv(k, map) : k);
-                    if (PAIRS) st_stream(vdst + g, s_rvals[s]);
-                } else {
-                    atomicOr(a.status, ST_RANGE);
-                }
+                st_stream(dst + g, desc.xout ? map_inv(k, map) : k);
+                if (PAIRS) st_stream(vdst + g, s_rvals[s]);
             }
         }
         __syncthreads();   // the tile buffers are reused by later iterations

@@ -95,12 +95,13 @@ inline bool onesweep_config_fits(int w, bool pairs, int block, int kpt, int d, i
 }
 
 // Compiled ranking variants: ballot for every width, shared match masks for
-// widths up to 8, match.any for 8-bit digits.
+// widths up to 8, match.any for 8-bit digits; adaptive (4: match masks or
+// match.any, chosen per pass) for 8-bit digits.
 inline bool onesweep_rank_supported(int rank, int d) {
-    return rank == 2 || (rank == 1 && d == 8) || (rank == 3 && d <= 8);
+    return rank == 2 || (rank == 1 && d == 8) || (rank == 3 && d <= 8) || (rank == 4 && d == 8);
 }
 inline bool onesweep_rank_fits(int rank, int block, int kpt, int w, bool pairs, int d) {
-    return rank != 3 || match_masks_fit(block, kpt, w, pairs, d);
+    return (rank != 3 && rank != 4) || match_masks_fit(block, kpt, w, pairs, d);
 }
 
 // Defined in radix32k.cu, radix32p.cu, radix64k.cu, radix64p.cu.

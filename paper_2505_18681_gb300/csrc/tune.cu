@@ -74,7 +74,7 @@ Genome random_genome(Rng& r, int tins_hi) {
     g.algo = r.unit() < 0.5 ? EVOSORT_ALGO_RADIX : EVOSORT_ALGO_MERGE;
     g.d = r.range(4, 11);
     g.shape = r.range(0, kNShapes - 1);
-    g.rank = r.range(1, 3);
+    g.rank = r.range(1, 4);
     g.tins = r.range(2, tins_hi);
     return g;
 }
@@ -224,7 +224,7 @@ evosort_status evosort_ga_search(const evosort_ga_config* cfg, int key_bytes, ev
         if (!c.allow_merge) g.algo = EVOSORT_ALGO_RADIX;
     }
     // seed the defaults so the tuned result is never worse than the plain path
-    pop[0] = Genome{EVOSORT_ALGO_RADIX, 8, w == 4 ? 2 : 3, 3, 32};
+    pop[0] = Genome{EVOSORT_ALGO_RADIX, 8, w == 4 ? 2 : 3, 4, 32};
     std::vector<float> fit(c.population);
     for (int gen = 0; gen < c.generations; ++gen) {
         for (int i = 0; i < c.population; ++i) {

@@ -101,12 +101,19 @@ def test_host_batch_rejects_bad_arguments_without_a_gpu(lib):
 
 
 @pytest.mark.parametrize("field,value", [("digit_bits", 3), ("digit_bits", 12), ("algo", 7),
-                                         ("rank_mode", 4), ("rank_mode", -1), ("insertion_threshold", 1),
+                                         ("rank_mode", 5), ("rank_mode", -1), ("insertion_threshold", 1),
                                          ("insertion_threshold", 4096), ("block_size", 100)])
 def test_rejects_bad_params(lib, field, value):
     p = _params(lib, **{field: value})
     assert lib.evosort_sort(FAKE, 10, 0, ctypes.byref(p)) == 1
     assert lib.evosort_workspace_bytes(1000, 0, 0, ctypes.byref(p)) == 0
+
+
+def test_adaptive_ranking_needs_8_bit_digits(lib):
+    for d in (4, 6, 7, 9, 11):
+        p = _params(lib, rank_mode=4, digit_bits=d)
+        assert lib.evosort_sort(FAKE, 10, 0, ctypes.byref(p)) == 1
+    assert b"rank_mode" in lib.evosort_last_error()
 
 
 def test_workspace_bytes_grows_with_n(lib):

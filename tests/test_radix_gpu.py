@@ -122,7 +122,7 @@ def vw_of(block, kpt, w, pairs, d):
 
 
 @pytest.mark.parametrize("shape", [(256, 8), (256, 16), (512, 8), (512, 16), (512, 32), (1024, 8), (1024, 16)])
-@pytest.mark.parametrize("rank", [1, 2, 3])
+@pytest.mark.parametrize("rank", [1, 2, 3, 4])
 @pytest.mark.parametrize("d", [6, 8, 11])
 def test_tile_shapes_and_ranking(evo, shape, rank, d):
     """Every compiled tile shape and ranking variant; shapes whose tile does
@@ -135,8 +135,9 @@ def test_tile_shapes_and_ranking(evo, shape, rank, d):
         x = gen("zipf" if dtype == torch.int64 else "uniform", 150_011, dtype)
         for pairs in (False, True):
             runner = run_pairs if pairs else run_keys
-            compiled = rank == 2 or (rank == 1 and d == 8) or (rank == 3 and d <= 8)
-            masks_fit = rank != 3 or block // 32 * vw_of(block, kpt, w, pairs, d) * (1 << d) * 4 <= block * kpt * w
+            compiled = rank == 2 or (rank in (1, 4) and d == 8) or (rank == 3 and d <= 8)
+            masks_fit = rank not in (3, 4) or \
+                block // 32 * vw_of(block, kpt, w, pairs, d) * (1 << d) * 4 <= block * kpt * w
             if compiled and masks_fit and tile_fits(block, kpt, w, pairs, d, rank):
                 runner(evo, x, **kw)
             else:
@@ -230,3 +231,56 @@ def test_digit_prefix_above_2_24(evo, dtype):
     pick = gen("uniform", n, torch.int64, seed=12).remainder(10) != 0
     x = torch.where(pick, torch.full_like(x, 3), x)
     run_keys(evo, x)
+
+
+ADAPT_N = 3_000_017   # above the size where adaptive ranking starts (2^21 keys)
+
+
+@pytest.mark.parametrize("dist", ["gaussian", "distinct16", "zipf", "uniform1000", "sorted", "uniform"])
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64, torch.float64], ids=str)
+def test_adaptive_ranking(evo, dist, dtype):
+    """Rank mode 4 (the default): every pass launches the match-mask and the
+    match.any kernel and exactly one of them runs; the result is the oracle's,
+    for keys and for stable pairs."""
+    x = gen(dist, ADAPT_N, dtype, seed=9)
+    evo.profile(True)
+    try:
+        run_keys(evo, x, algo="radix", rank_mode=4, digit_bits=8)
+        recs = [r for r in evo.profile_read() if r["kind"] == "radix_onesweep"]
+    finally:
+        evo.profile(False)
+    passes = {}
+    for r in recs:
+        passes.setdefault(r["pass"], []).append(r)
+    assert len(passes) == 8 * x.element_size() // 8
+    for p, rs in passes.items():
+        assert sorted(r["rank"] for r in rs) == [1, 3]
+        assert sum(r["active"] for r in rs) <= 1
+    run_pairs(evo, x, algo="radix", rank_mode=4, digit_bits=8)
+
+
+def test_adaptive_ranking_choice_per_pass(evo):
+    """Gaussian int64 keys (sd 1e6): the five top bytes take two values, so
+    passes 3..7 run match.any; passes 0..2 (spread digits, the first pass in
+    input order) run match masks."""
+    x = gen("gaussian", ADAPT_N, torch.int64, seed=9)
+    y = torch.empty_like(x)
+    evo.profile(True)
+    try:
+        evo.sort(x, out=y, algo="radix", rank_mode=4, digit_bits=8)
+        evo.sync()
+        recs = [r for r in evo.profile_read() if r["kind"] == "radix_onesweep" and r["active"]]
+    finally:
+        evo.profile(False)
+    assert {r["pass"]: r["rank"] for r in recs} == {0: 3, 1: 3, 2: 3, 3: 1, 4: 1, 5: 1, 6: 1, 7: 1}
+
+
+def test_below_adaptive_size_single_launch_per_pass(evo):
+    x = gen("gaussian", 100_003, torch.int64)
+    evo.profile(True)
+    try:
+        run_keys(evo, x, algo="radix", rank_mode=4, digit_bits=8)
+        recs = [r for r in evo.profile_read() if r["kind"] == "radix_onesweep"]
+    finally:
+        evo.profile(False)
+    assert len(recs) == 8 and all(r["rank"] == 0 for r in recs)

@@ -68,7 +68,7 @@ def test_first_generation_holds_the_defaults(evo):
         seen.append(p)
         return landscape(p, best)
     evo.ga_search(record, key_bytes=8, seed=1, generations=1)
-    assert {"algo": 0, "digit_bits": 8, "rank_mode": 3} .items() <= seen[0].items()
+    assert {"algo": 0, "digit_bits": 8, "rank_mode": 4}.items() <= seen[0].items()
 
 
 def test_merge_only_when_allowed(evo):
