@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--dtype", default="int64", choices=["int32", "int64", "uint32", "uint64"])
     ap.add_argument("--dists", default=",".join(DISTS))
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-par-sample", type=int, default=1 << 24,
+                    help="keys per distribution for the multithreaded CPU baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--params", default="auto", choices=["auto", "plain", "tuned"])
     ap.add_argument("--digit-bits", type=int, default=0)
@@ -201,6 +203,24 @@ def oracle_sample_run(dists, dtype_name, sample, seed=42):
     return len(arrays) * sample, dt
 
 
+def parallel_sample_run(dists, dtype_name, sample, seed=42):
+    """The paper-shaped multithreaded CPU radix sort on every host core, on a
+    bounded sample of each distribution: (keys, seconds, threads)."""
+    import torch
+
+    import oracle
+    from paper_2505_18681_gb300 import inputs
+    tdt = getattr(torch, dtype_name)
+    arrays = [inputs.generate(d, sample, tdt, seed=seed, device="cpu").numpy() for d in dists]
+    oracle.parallel_radix_sort(arrays[0][:1024])   # load, spawn threads once
+    used = 1
+    t0 = time.perf_counter()
+    for a in arrays:
+        _, used = oracle.parallel_radix_sort(a)
+    dt = time.perf_counter() - t0
+    return len(arrays) * sample, dt, used
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -320,15 +340,17 @@ def main():
     sampler.start()
     barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+    # one event per step boundary: the K-step total and each step's time
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for k in range(args.steps):
         step(params)
-    e1.record(stream)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
+    e0, e1 = evs[0], evs[-1]
+    per_step = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
     launches = evo.kernel_launches() - launches0
     recs = evo.profile_read()
     evo.profile(False)
@@ -377,7 +399,9 @@ def main():
     act = [r for r in recs if r["kind"] == "radix_onesweep" and r["active"]]
     ach = (sum(r["bytes"] for r in act) / 1e9) / (sum(r["ms"] for r in act) * 1e-3) if act else 0.0
     peak, peak_src = measured_peaks()
-    tpk = traffic_from_profiles(kernel_hash())
+    # the committed capture is of the 64-bit keys-only kernel; other key
+    # widths have no measured traffic
+    tpk = traffic_from_profiles(kernel_hash()) if w == 8 else None
     traffic = None
     if tpk is not None and act:
         traffic = tpk * act[0]["items"]
@@ -400,17 +424,23 @@ def main():
     if not args.no_e2e and rank == 0 or (not args.no_e2e and ws > 1):
         e2e = measure_e2e(evo, xs, out, params, stream, n, w, args, barrier, ws, dev, mode == "tuned")
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         k, t = oracle_sample_run(dists, args.dtype, args.cpu_sample)
         cpu = {"value": k / t / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
                "sample": "%d keys of each of the %d distributions (single-threaded C LSD radix, 8-bit digits)"
                % (args.cpu_sample, len(dists))}
+        k, t, used = parallel_sample_run(dists, args.dtype, args.cpu_par_sample)
+        cpu_par = {"value": k / t / 1e9, "unit": "GKeys/s", "cores": used,
+                   "kind": "paper-shaped multithreaded CPU LSD radix (per-thread histograms, thread-wise offsets)",
+                   "sample": "%d keys of each of the %d distributions, all online host cores"
+                   % (args.cpu_par_sample, len(dists))}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GKeys/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "step_ms": {"min": per_step[0], "median": statistics.median(per_step), "max": per_step[-1]},
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": "nine-distribution %s sort, %d keys per array (one step sorts all nine)"
                        % (args.dtype, n), "n_per_array": n, "dists": dists, "params": mode,
@@ -430,6 +460,7 @@ def main():
             "kernel_time_share": shares,
             "per_dist_ms": per_dist,
             "cpu_baseline": cpu,
+            "cpu_parallel": cpu_par,
             "clocks": clocks,
             "gpu_launches": launches,
         }

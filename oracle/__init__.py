@@ -12,7 +12,11 @@ Functions take and return numpy arrays:
 * ``merge_sort(keys, values=None, chunk_size=32)`` — O2, bottom-up mergesort
   with insertion-sorted base chunks (Algorithm 3);
 * ``segmented_sort(keys, offsets)`` — O1 per segment;
-* ``ordered_bits(raw_bits, dtype)`` — the total-order map on key bits.
+* ``ordered_bits(raw_bits, dtype)`` — the total-order map on key bits;
+* ``parallel_radix_sort(keys, threads=0)`` — the CPU baseline, not an oracle:
+  the paper's multithreaded radix sort shape (per-thread histograms and
+  thread-wise offsets, Algorithms 4a/4b) on the host cores
+  (``oracle/cpu_parallel.c``, checked against O1 in the tests).
 
 Parity status: pinned (see ``tests/test_oracle.py``): brute force over all
 permutations of tiny inputs, a selection sort written from the definition of
@@ -42,8 +46,12 @@ _DT_CODE = {
     np.dtype(np.float64): 5,
 }
 
+_PAR_SRC = os.path.join(_HERE, "cpu_parallel.c")
+_PAR_LIB_PATH = os.path.join(_BUILD, "libcpu_parallel.so")
+
 _lock = threading.Lock()
 _lib = None
+_par_lib = None
 
 
 def build(force: bool = False) -> str:
@@ -56,6 +64,13 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
                                "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
+    par_stale = force or not os.path.exists(_PAR_LIB_PATH) or (
+        os.path.getmtime(_PAR_LIB_PATH) < os.path.getmtime(_PAR_SRC))
+    if par_stale:
+        tmp = _PAR_LIB_PATH + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-pthread",
+                               "-o", tmp, _PAR_SRC])
+        os.replace(tmp, _PAR_LIB_PATH)
     return _LIB_PATH
 
 
@@ -143,3 +158,23 @@ def ordered_bits(raw: int, dtype) -> int:
 def set_fault(code: int) -> None:
     """Plant a known mistake in the oracle (self-tests of the pins only)."""
     _load().oracle_set_fault(int(code))
+
+
+def parallel_radix_sort(keys: np.ndarray, threads: int = 0):
+    """CPU baseline: returns (sorted keys, threads used).  threads <= 0 uses
+    every online CPU."""
+    global _par_lib
+    with _lock:
+        if _par_lib is None:
+            build()
+            lib = ctypes.CDLL(_PAR_LIB_PATH)
+            lib.cpu_parallel_radix_sort.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                                    ctypes.c_int, ctypes.c_int]
+            lib.cpu_parallel_radix_sort.restype = ctypes.c_int
+            _par_lib = lib
+    keys = np.ascontiguousarray(keys)
+    out = np.empty_like(keys)
+    used = _par_lib.cpu_parallel_radix_sort(_ptr(keys), _ptr(out), keys.size, _code(keys), int(threads))
+    if used < 0:
+        raise MemoryError("cpu_parallel_radix_sort failed")
+    return out, used

@@ -367,3 +367,30 @@ def test_segmented_generator_all_widths():
         for i in range(0, 50, 7):
             a, b = int(offs[i]), int(offs[i + 1])
             assert np.array_equal(out[a:b], np.sort(keys.numpy()[a:b]))
+
+
+# ---- the paper-shaped multithreaded CPU baseline, against the oracle ---------
+@pytest.mark.parametrize("dtype", [np.int32, np.int64, np.uint32, np.uint64, np.float32, np.float64])
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_cpu_parallel_baseline_matches_oracle(dtype, threads):
+    import oracle
+    rng = np.random.default_rng(17)
+    for n in (0, 1, 2, 7, 1000, 100_003):
+        if np.dtype(dtype).kind == "f":
+            x = rng.uniform(-1e6, 1e6, n).astype(dtype)
+            if n > 10:
+                dup = rng.integers(0, n, n // 7)
+                x[dup] = x[rng.integers(0, n, dup.size)]    # duplicates
+                x[3] = -0.0
+                x[5] = 0.0
+                x[8] = np.nan
+                x[9] = -np.nan
+        else:
+            info = np.iinfo(dtype)
+            x = rng.integers(info.min, info.max, n, dtype=dtype, endpoint=True)
+            if n > 10:
+                x[::5] = x[1]                                # duplicates
+        got, used = oracle.parallel_radix_sort(x, threads)
+        assert used == max(1, min(threads, n))
+        want = oracle.radix_sort(x)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
