@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--kpt", type=int, default=0)
     ap.add_argument("--rank-mode", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=1 << 23, help="keys per distribution for the oracle")
-    ap.add_argument("--workload", default="nine", choices=["nine", "floatpairs", "segmented", "u32big"],
+    ap.add_argument("--sizes", default="1e7,1e8,1e9,5e9", help="paper9 workload: array sizes")
+    ap.add_argument("--workload", default="nine", choices=["nine", "floatpairs", "segmented", "u32big", "paper9"],
                     help="nine: the headline workload; the others measure the other configurations")
     ap.add_argument("--segments", type=int, default=100_000)
     return ap.parse_args()
@@ -558,6 +559,51 @@ def other_workload(args):
                     roofline={"bound": "hbm", "kernel": "radix_onesweep (pairs)", "achieved": ach, "peak": peak,
                               "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src},
                     clocks=clocks, gpu_launches=evo.kernel_launches() - launches0)
+    elif args.workload == "paper9":
+        # the paper's nine int32 distributions over a size sweep, five timed
+        # sorts each (the paper's protocol: min / median / max of 5), tuned
+        # int32 table through the dispatcher
+        sizes = [int(float(v)) for v in args.sizes.split(",")]
+        table = os.path.join(ROOT, "paper_2505_18681_gb300", "tuned", "gb300_int32.txt")
+        evo.table_clear()
+        if os.path.exists(table):
+            evo.table_load(table)
+        res = {}
+        tot_keys = tot_ms = 0.0
+        launches0 = evo.kernel_launches()
+        sampler.start()
+        for d in inputs.PAPER_DISTRIBUTIONS:
+            res[d] = {}
+            for n in sizes:
+                x = inputs.generate(d, n, torch.int32, seed=42, device="cuda")
+                y = torch.empty_like(x)
+                pd, _ = evo.plan(x, stream=stream)
+                p = evo.make_params(stream=stream, **pd)
+                for _ in range(max(args.warmup, 1)):
+                    evo.sort(x, out=y, params=p)
+                ts = []
+                for _ in range(5):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    evo.sort(x, out=y, params=p)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                evo.sync()
+                ts.sort()
+                res[d]["%.0e" % n] = {"min_ms": round(ts[0], 4), "median_ms": round(ts[2], 4),
+                                      "max_ms": round(ts[4], 4)}
+                tot_keys += n
+                tot_ms += ts[2]
+                del x, y
+                torch.cuda.empty_cache()
+        clocks = sampler.stop()
+        evo.table_clear()
+        line.update(value=tot_keys / (tot_ms * 1e-3) / 1e9, ms_per_step=tot_ms, dtype="i32",
+                    config={"workload": "the paper's nine int32 distributions in [-1e9, 1e9], sizes %s, "
+                            "median of 5 sorts each, tuned int32 table" % args.sizes},
+                    per_dist=res, clocks=clocks, gpu_launches=evo.kernel_launches() - launches0)
     elif args.workload == "u32big":
         n = 10_000_000_000 if args.n == 1_000_000_000 else args.n
         x = inputs.generate("uniform", n, torch.uint32, seed=42, device="cuda")

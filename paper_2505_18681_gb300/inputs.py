@@ -23,6 +23,29 @@ Distributions (names used by the tests, the benchmark and the tuner):
 * ``uniform1000``    integers uniform in [0, 1000)
 * ``float_mix``      float64 uniform in [-1e6, 1e6], 1% of positions copied
   from other positions, then 0.1% each of -0.0, +0.0, +qNaN, -qNaN
+
+The paper's own nine integer distributions (its Section 5 data-distribution
+tests), mapped to [-1e9, 1e9] as the paper describes and truncated toward
+zero to integers; counter-based draws stand in for NumPy's generator, so the
+shapes match and the exact values do not:
+
+* ``paper_uniform``        integers uniform in [-1e9, 1e9)
+* ``paper_normal``         N(0, 1e8) clipped to [-1e9, 1e9]
+* ``paper_exponential``    Exp(scale 1e9) clipped to [0, 2e9], minus 1e9
+* ``paper_power``          power law with a = 0.5 (u^(1/a)) scaled to [-1e9, 1e9]
+* ``paper_beta``           Beta(2, 5) scaled to [-1e9, 1e9]
+* ``paper_sparse``         zero, except each position with probability 0.1 is
+  a uniform integer in [-1e9, 1e9)
+* ``paper_clustered``      one of 10 evenly spaced centres in [-1e9, 1e9] plus
+  N(0, 1e8), clipped
+* ``paper_nearly_sorted``  the evenly spaced ramp from -1e9 to 1e9, each
+  position replaced with probability 0.1 by a uniform integer
+* ``paper_duplicates``     each element one of n // 10 seeded uniform integers
+
+Distributions drawn through log / cos (``gaussian``, ``paper_normal``,
+``paper_exponential``, ``paper_beta``, ``paper_clustered``) may differ in a
+rare last integer step between devices; every test sorts the exact device
+input, so this never matters.
 """
 from __future__ import annotations
 
@@ -47,8 +70,11 @@ _CHUNK = 1 << 26
 DISTRIBUTIONS = ("uniform", "gaussian", "sorted", "reverse", "nearly_sorted",
                  "distinct16", "zipf", "equal", "uniform1000")
 
+PAPER_DISTRIBUTIONS = ("paper_uniform", "paper_normal", "paper_exponential", "paper_power", "paper_beta",
+                       "paper_sparse", "paper_clustered", "paper_nearly_sorted", "paper_duplicates")
+
 _STREAM_ID = {name: i + 1 for i, name in enumerate(
-    DISTRIBUTIONS + ("uniform_paper", "float_mix", "seglen", "segkeys", "aux"))}
+    DISTRIBUTIONS + ("uniform_paper", "float_mix", "seglen", "segkeys", "aux") + PAPER_DISTRIBUTIONS)}
 
 
 def _lsr(z: torch.Tensor, k: int) -> torch.Tensor:
@@ -173,7 +199,70 @@ def generate(dist: str, n: int, dtype=torch.int64, seed: int = 42, device="cpu")
         v = raw64(st, 0, 1, "cpu").item()
         return _fill(n, dtype, device,
                      lambda s, c: torch.full((c,), v, dtype=torch.int64, device=device))
+    if dist in PAPER_DISTRIBUTIONS:
+        return _fill(n, dtype, device, _paper_fn(dist, n, seed, st, device))
     raise ValueError("unknown distribution %r" % dist)
+
+
+def raw64_at(state: int, idx: torch.Tensor) -> torch.Tensor:
+    """SplitMix64 outputs at arbitrary positions ``idx`` (int64) of a stream."""
+    return _mix((idx + 1) * _GOLDEN + state)
+
+
+def _paper_fn(dist, n, seed, st, device):
+    """Chunk filler for the paper's nine distributions (values as int64)."""
+    def sub(j):   # independent sub-streams of this distribution
+        return stream_state(seed, 1000 * _STREAM_ID[dist] + j)
+
+    def u(j, s, c):
+        return unit_double(raw64(sub(j), s, c, device))
+
+    def randint(j, s, c):   # uniform in [-1e9, 1e9)
+        return _bounded(raw64(sub(j), s, c, device), 2_000_000_000) - 1_000_000_000
+
+    def normal(j, s, c):
+        return torch.sqrt(-2.0 * torch.log1p(-u(j, s, c))) * torch.cos(2.0 * math.pi * u(j + 1, s, c))
+
+    def to_int(x):
+        return torch.trunc(x).to(torch.int64)
+
+    if dist == "paper_uniform":
+        return lambda s, c: randint(0, s, c)
+    if dist == "paper_normal":
+        return lambda s, c: to_int(torch.clamp(normal(0, s, c) * 1e8, -1e9, 1e9))
+    if dist == "paper_exponential":
+        return lambda s, c: to_int(torch.clamp(-torch.log1p(-u(0, s, c)) * 1e9, 0.0, 2e9) - 1e9)
+    if dist == "paper_power":
+        return lambda s, c: to_int(u(0, s, c) ** 2 * 2e9 - 1e9)
+    if dist == "paper_beta":
+        def beta(s, c):
+            # Beta(2, 5) = G2 / (G2 + G5), Gamma(k) a sum of k unit exponentials
+            e = [-torch.log1p(-u(j, s, c)) for j in range(7)]
+            g2 = e[0] + e[1]
+            g5 = e[2] + e[3] + e[4] + e[5] + e[6]
+            return to_int(g2 / (g2 + g5) * 2e9 - 1e9)
+        return beta
+    if dist == "paper_sparse":
+        return lambda s, c: torch.where(u(0, s, c) < 0.1, randint(1, s, c), torch.zeros_like(randint(1, s, c)))
+    if dist == "paper_clustered":
+        def clustered(s, c):
+            k = _bounded(raw64(sub(0), s, c, device), 10).to(torch.float64)
+            centre = -1e9 + k * (2e9 / 9.0)
+            return to_int(torch.clamp(centre + normal(1, s, c) * 1e8, -1e9, 1e9))
+        return clustered
+    if dist == "paper_nearly_sorted":
+        def nearly(s, c):
+            i = torch.arange(s, s + c, dtype=torch.float64, device=device)
+            ramp = to_int(-1e9 + i * (2e9 / max(n - 1, 1)))
+            return torch.where(u(0, s, c) < 0.1, randint(1, s, c), ramp)
+        return nearly
+    if dist == "paper_duplicates":
+        m = max(n // 10, 1)
+        def dup(s, c):
+            k = _bounded(raw64(sub(0), s, c, device), m)
+            return _bounded(raw64_at(sub(1), k), 2_000_000_000) - 1_000_000_000
+        return dup
+    raise ValueError(dist)
 
 
 def _disjoint_swaps(x: torch.Tensor, m: int, seed: int, device) -> None:

@@ -281,6 +281,46 @@ def test_invariants_on_workload_distributions(dist):
         assert np.array_equal(k, k2) and np.array_equal(vv, v2)
 
 
+@pytest.mark.parametrize("dist", ["paper_uniform", "paper_normal", "paper_exponential", "paper_power",
+                                  "paper_beta", "paper_sparse", "paper_clustered", "paper_nearly_sorted",
+                                  "paper_duplicates"])
+def test_invariants_on_paper_distributions(dist):
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    x = inputs.generate(dist, 3001, torch.int32, seed=42).numpy()
+    v = np.arange(x.size, dtype=np.uint32)
+    k, vv = oracle.radix_sort(x, v)
+    check_invariants(x, k, v, vv)
+    assert np.array_equal(k, np.sort(x, kind="stable"))
+
+
+def test_paper_distribution_shapes():
+    """The paper's nine int32 distributions have the moments and structure
+    their definitions fix (100,000 draws; tolerances several standard errors)."""
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    n = 100_000
+    g = {d: inputs.generate(d, n, torch.int32, seed=7).numpy().astype(np.float64)
+         for d in inputs.PAPER_DISTRIBUTIONS}
+    for d, x in g.items():
+        assert x.min() >= -1e9 and x.max() <= 1e9, d
+    assert abs(g["paper_uniform"].mean()) < 1e7
+    assert abs(g["paper_uniform"].std() - 2e9 / math.sqrt(12)) < 1e7
+    assert abs(g["paper_normal"].mean()) < 2e6 and abs(g["paper_normal"].std() - 1e8) < 2e6
+    # E[min(X, 2e9)] - 1e9 for X ~ Exp(1e9)
+    assert abs(g["paper_exponential"].mean() - (1e9 * (1 - math.exp(-2)) - 1e9)) < 1e7
+    assert abs(g["paper_power"].mean() - (2e9 / 3 - 1e9)) < 1e7           # E[U^2] = 1/3
+    assert abs(g["paper_beta"].mean() - (2e9 * 2 / 7 - 1e9)) < 5e6         # E[Beta(2,5)] = 2/7
+    assert abs((g["paper_sparse"] == 0).mean() - 0.9) < 0.01
+    near = g["paper_clustered"]
+    centres = -1e9 + np.arange(10) * (2e9 / 9)
+    dist_to_centre = np.min(np.abs(near[:, None] - centres[None, :]), axis=1)
+    assert np.mean(dist_to_centre < 3e8) > 0.99                               # 3 sigma
+    ns = g["paper_nearly_sorted"]
+    assert 0.88 < np.mean(ns[1:] >= ns[:-1]) < 0.93
+    assert abs(len(np.unique(g["paper_duplicates"])) - n // 10) < n // 100
+
+
 def test_float_mix_invariants():
     import torch
     from paper_2505_18681_gb300 import inputs

@@ -284,3 +284,25 @@ def test_below_adaptive_size_single_launch_per_pass(evo):
     finally:
         evo.profile(False)
     assert len(recs) == 8 and all(r["rank"] == 0 for r in recs)
+
+
+PAPER_DISTS = ["paper_uniform", "paper_normal", "paper_exponential", "paper_power", "paper_beta",
+               "paper_sparse", "paper_clustered", "paper_nearly_sorted", "paper_duplicates"]
+
+
+@pytest.mark.parametrize("dist", PAPER_DISTS)
+def test_paper_distributions_int32(evo, dist):
+    """The paper's nine int32 distributions, through the dispatcher's choice
+    with the tuned int32 table and through the defaults, keys and pairs."""
+    import os
+    x = gen(dist, ADAPT_N, torch.int32, seed=3)
+    run_keys(evo, x, algo="radix")
+    run_pairs(evo, x, algo="radix")
+    table = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2505_18681_gb300",
+                         "tuned", "gb300_int32.txt")
+    evo.table_clear()
+    evo.table_load(table)
+    try:
+        run_keys(evo, x)
+    finally:
+        evo.table_clear()
