@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--rank-mode", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=1 << 23, help="keys per distribution for the oracle")
     ap.add_argument("--sizes", default="1e7,1e8,1e9,5e9", help="paper9 workload: array sizes")
-    ap.add_argument("--workload", default="nine", choices=["nine", "floatpairs", "segmented", "u32big", "paper9"],
+    ap.add_argument("--workload", default="nine",
+                    choices=["nine", "floatpairs", "segmented", "u32big", "paper9", "friendster"],
                     help="nine: the headline workload; the others measure the other configurations")
     ap.add_argument("--segments", type=int, default=100_000)
     return ap.parse_args()
@@ -604,6 +605,35 @@ def other_workload(args):
                     config={"workload": "the paper's nine int32 distributions in [-1e9, 1e9], sizes %s, "
                             "median of 5 sorts each, tuned int32 table" % args.sizes},
                     per_dist=res, clocks=clocks, gpu_launches=evo.kernel_launches() - launches0)
+    elif args.workload == "friendster":
+        # stand-in for the paper's real-data test: 3,612,134,270 int32 node
+        # ids of a heavy-tailed graph, one sort, tuned int32 table
+        n = inputs.FRIENDSTER_N if args.n == 1_000_000_000 else args.n
+        table = os.path.join(ROOT, "paper_2505_18681_gb300", "tuned", "gb300_int32.txt")
+        evo.table_clear()
+        if os.path.exists(table):
+            evo.table_load(table)
+        x = inputs.generate("friendster_like", n, torch.int32, seed=42, device="cuda")
+        y = torch.empty_like(x)
+        pd, cls = evo.plan(x, stream=stream)
+        p = evo.make_params(stream=stream, **pd)
+        launches0 = evo.kernel_launches()
+        evo.profile(True)
+        sampler.start()
+        ms = _time_steps(lambda: evo.sort(x, out=y, params=p), args.steps, args.warmup, stream)
+        clocks = sampler.stop()
+        recs = [r for r in evo.profile_read() if r["kind"] == "radix_onesweep" and r["active"]]
+        evo.profile(False)
+        evo.sync()
+        evo.table_clear()
+        ach = sum(r["bytes"] for r in recs) / 1e9 / (sum(r["ms"] for r in recs) * 1e-3) if recs else 0.0
+        line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="i32",
+                    config={"workload": "%d int32 node ids in [101, 124836179] with heavy-tailed frequency "
+                            "(stand-in for the paper's Friendster endpoint column), one sort" % n,
+                            "class": cls, "plan": pd},
+                    roofline={"bound": "hbm", "kernel": "radix_onesweep", "achieved": ach, "peak": peak,
+                              "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src},
+                    clocks=clocks, gpu_launches=evo.kernel_launches() - launches0)
     elif args.workload == "u32big":
         n = 10_000_000_000 if args.n == 1_000_000_000 else args.n
         x = inputs.generate("uniform", n, torch.uint32, seed=42, device="cuda")

@@ -191,12 +191,15 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
 // K2: exclusive prefix sum of each pass's digit counts, trivial-pass test and
 // the buffer chain.  One CTA of 1024 threads.
 // ---------------------------------------------------------------------------
-// Adaptive ranking (rank mode 4): the first active pass sees the keys in input
-// order and ranks with shared match masks; a later pass ranks with match.any
-// when its digit is concentrated (sum over digits of (count / n)^2 above
-// 1/32: most lanes of a warp then share a few digits, which serialises the
-// match masks' shared atomics), else with match masks.
+// Adaptive ranking (rank mode 4): a pass ranks with match.any when its digit
+// is concentrated, else with shared match masks.  Concentration is the sum
+// over digits of (count / n)^2: when it is high, most lanes of a warp share a
+// few digits, which serialises the match masks' shared atomics.  A later pass
+// sees keys already grouped by the lower digits, so equal digits sit together
+// and 1/32 is the threshold; the first pass to run sees the input order, where
+// match.any only pays once one digit holds most keys (threshold 1/4).
 constexpr double kConcentrated = 1.0 / 32.0;
+constexpr double kConcentratedFirst = 1.0 / 4.0;
 
 static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int inplace) {
     __shared__ unsigned long long s_scr[33];
@@ -224,7 +227,8 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int w = 0; w < 32; ++w) t += s_sq[w];
-            s_conc[p] = t > kConcentrated * (double)a.n * (double)a.n;
+            const double nn = (double)a.n * (double)a.n;
+            s_conc[p] = (t > kConcentrated * nn ? 1 : 0) | (t > kConcentratedFirst * nn ? 2 : 0);
         }
         unsigned long long tot;
         unsigned long long ex = block_exclusive_scan<1024>(sum, s_scr, &tot);
@@ -257,7 +261,7 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
             }
             pd.xin = (k == 0);
             pd.xout = (k == e - 1);
-            pd.rank = (k > 0 && s_conc[active[k]]) ? 1 : 3;
+            pd.rank = (s_conc[active[k]] & (k > 0 ? 1 : 2)) ? 1 : 3;
             a.desc[active[k]] = pd;
         }
         int fix = FIX_NONE;

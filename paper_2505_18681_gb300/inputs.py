@@ -42,6 +42,15 @@ shapes match and the exact values do not:
   position replaced with probability 0.1 by a uniform integer
 * ``paper_duplicates``     each element one of n // 10 seeded uniform integers
 
+A stand-in for the paper's real-data test (the Friendster edge list's
+endpoint column, which is not available here):
+
+* ``friendster_like``  node ids in [101, 124,836,179] with a heavy-tailed
+  frequency: node rank k = floor(M u^3) over M = 65,608,366 nodes (density
+  proportional to k^(-2/3)), mapped to an id by a fixed bijection
+  k -> 101 + (k * 2654435761 mod 124,836,078), so frequent ids spread over
+  the range
+
 Distributions drawn through log / cos (``gaussian``, ``paper_normal``,
 ``paper_exponential``, ``paper_beta``, ``paper_clustered``) may differ in a
 rare last integer step between devices; every test sorts the exact device
@@ -73,8 +82,13 @@ DISTRIBUTIONS = ("uniform", "gaussian", "sorted", "reverse", "nearly_sorted",
 PAPER_DISTRIBUTIONS = ("paper_uniform", "paper_normal", "paper_exponential", "paper_power", "paper_beta",
                        "paper_sparse", "paper_clustered", "paper_nearly_sorted", "paper_duplicates")
 
+FRIENDSTER_N = 3_612_134_270        # endpoints in the paper's real-data test
+_FRIENDSTER_NODES = 65_608_366
+_FRIENDSTER_LO, _FRIENDSTER_HI = 101, 124_836_179
+
 _STREAM_ID = {name: i + 1 for i, name in enumerate(
-    DISTRIBUTIONS + ("uniform_paper", "float_mix", "seglen", "segkeys", "aux") + PAPER_DISTRIBUTIONS)}
+    DISTRIBUTIONS + ("uniform_paper", "float_mix", "seglen", "segkeys", "aux") + PAPER_DISTRIBUTIONS +
+    ("friendster_like",))}
 
 
 def _lsr(z: torch.Tensor, k: int) -> torch.Tensor:
@@ -201,6 +215,12 @@ def generate(dist: str, n: int, dtype=torch.int64, seed: int = 42, device="cpu")
                      lambda s, c: torch.full((c,), v, dtype=torch.int64, device=device))
     if dist in PAPER_DISTRIBUTIONS:
         return _fill(n, dtype, device, _paper_fn(dist, n, seed, st, device))
+    if dist == "friendster_like":
+        span = _FRIENDSTER_HI - _FRIENDSTER_LO   # 124,836,078; the multiplier is odd and coprime to it
+        def fr(s, c):
+            k = torch.floor(_FRIENDSTER_NODES * unit_double(raw64(st, s, c, device)) ** 3).to(torch.int64)
+            return _FRIENDSTER_LO + (k * 2654435761) % span
+        return _fill(n, dtype, device, fr)
     raise ValueError("unknown distribution %r" % dist)
 
 

@@ -321,6 +321,24 @@ def test_paper_distribution_shapes():
     assert abs(len(np.unique(g["paper_duplicates"])) - n // 10) < n // 100
 
 
+def test_friendster_like_shape():
+    """Ids in the paper's node-id range, heavy-tailed: the most frequent id
+    far above the mean count, and the most frequent ids holding the share of
+    draws the rank law fixes."""
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    x = inputs.generate("friendster_like", 200_000, torch.int32, seed=42).numpy()
+    assert x.min() >= 101 and x.max() <= 124_836_179
+    _, counts = np.unique(x, return_counts=True)
+    assert counts.max() > 50 * counts.mean()
+    top = np.sort(counts)[::-1]
+    # P(rank < K) = (K / M)^(1/3): the 100 lowest ranks hold about 1.15% of the
+    # draws, 20 times what 100 uniformly drawn ids would
+    assert top[:100].sum() > 0.008 * x.size
+    k, vv = oracle.radix_sort(x, np.arange(x.size, dtype=np.uint32))
+    check_invariants(x, k, np.arange(x.size, dtype=np.uint32), vv)
+
+
 def test_float_mix_invariants():
     import torch
     from paper_2505_18681_gb300 import inputs

@@ -287,7 +287,7 @@ def test_below_adaptive_size_single_launch_per_pass(evo):
 
 
 PAPER_DISTS = ["paper_uniform", "paper_normal", "paper_exponential", "paper_power", "paper_beta",
-               "paper_sparse", "paper_clustered", "paper_nearly_sorted", "paper_duplicates"]
+               "paper_sparse", "paper_clustered", "paper_nearly_sorted", "paper_duplicates", "friendster_like"]
 
 
 @pytest.mark.parametrize("dist", PAPER_DISTS)
