@@ -139,11 +139,11 @@ evosort_status evosort_sort_pairs_to(const void* keys_in, const uint32_t* values
  * to the device, sorted there by the device path with params p (AUTO and a
  * non-empty table: the dispatcher's parameters for that array, classified
  * from a strided sample read on the host when the call is made, so the input
- * must already hold its keys then), and copied back.  The copy of array
- * i+1 to the device and of array i-1 back to the host run, one after the
- * other on one internal stream, while array i is sorted on p->stream,
- * through two device slots of max(n[i]) keys allocated from the
- * stream-ordered pool for the call.  The whole batch is ordered after earlier work on p->stream, and
+ * must already hold its keys then), and copied back.  The copies of
+ * array i+1 to the device and of array i-1 back to the host run on two
+ * internal streams while array i is sorted on p->stream, through three
+ * device slots of max(n[i]) keys allocated from the stream-ordered pool for
+ * the call.  The whole batch is ordered after earlier work on p->stream, and
  * later work on p->stream waits for all of it: evosort_sync(p->stream) or a
  * stream synchronisation makes the host outputs ready.  Host buffers should
  * be page-locked (cudaHostAlloc / cudaHostRegister): pageable buffers are

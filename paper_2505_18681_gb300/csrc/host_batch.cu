@@ -1,11 +1,7 @@
-// Sort of arrays held in host memory: two device slots and one copy stream
-// beside the caller's stream.  The copies run one at a time, in the order
-// upload(0), upload(1), download(0), upload(2), download(1), ..., so the sort
-// of array i (on the caller's stream) overlaps the upload of array i+1 and the
-// download of array i-1.  One copy at a time because on the host link of this
-// machine an upload and a download running together each fell to about a
-// fifth of their speed alone (40 GB/s each way against 211 / 193 GB/s), and
-// uploads split over several streams were slower than one.
+// Sort of arrays held in host memory: three device slots, an upload stream
+// and a download stream around the caller's stream, so that the upload of the
+// next array and the download of the previous one overlap the sort of the
+// current one on the GPU.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -19,28 +15,40 @@ using namespace evosort;
 
 namespace {
 
-constexpr int kSlots = 2;
+constexpr int kSlots = 3;
 
 struct BatchRes {
-    cudaStream_t xfer = nullptr;
-    cudaEvent_t ev_alloc = nullptr, ev_xfer_done = nullptr;
-    cudaEvent_t loaded[kSlots] = {}, sorted[kSlots] = {};
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_alloc = nullptr, ev_up_done = nullptr, ev_down_done = nullptr;
+    cudaEvent_t loaded[kSlots] = {}, sorted[kSlots] = {}, drained[kSlots] = {};
     bool ok = false;
 
     std::string create() {
-        cudaError_t e = cudaStreamCreateWithFlags(&xfer, cudaStreamNonBlocking);
-        cudaEvent_t* all[] = {&ev_alloc, &ev_xfer_done, &loaded[0], &loaded[1], &sorted[0], &sorted[1]};
+        cudaError_t e = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking);
+        cudaEvent_t* all[] = {&ev_start, &ev_alloc, &ev_up_done, &ev_down_done};
         for (cudaEvent_t* ev : all)
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        for (int k = 0; k < kSlots && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&loaded[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sorted[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&drained[k], cudaEventDisableTiming);
+        }
         ok = e == cudaSuccess;
         return ok ? std::string() : std::string(cudaGetErrorString(e));
     }
     // Streams and events are released once the work enqueued on them is done.
     ~BatchRes() {
-        cudaEvent_t evs[] = {ev_alloc, ev_xfer_done, loaded[0], loaded[1], sorted[0], sorted[1]};
+        cudaEvent_t evs[] = {ev_start, ev_alloc, ev_up_done, ev_down_done};
         for (cudaEvent_t ev : evs)
             if (ev) cudaEventDestroy(ev);
-        if (xfer) cudaStreamDestroy(xfer);
+        for (int k = 0; k < kSlots; ++k) {
+            if (loaded[k]) cudaEventDestroy(loaded[k]);
+            if (sorted[k]) cudaEventDestroy(sorted[k]);
+            if (drained[k]) cudaEventDestroy(drained[k]);
+        }
+        if (up) cudaStreamDestroy(up);
+        if (down) cudaStreamDestroy(down);
     }
 };
 
@@ -93,13 +101,10 @@ extern "C" evosort_status evosort_sort_host_batch(const void* const* keys_in, vo
     if (!r.ok) return fail(EVOSORT_ERR_CUDA, "stream/event creation: " + err);
 
     // slots come from the stream-ordered pool on the caller's stream; the copy
-    // stream starts after the allocation and after the caller's earlier work
+    // streams start after the allocation and after the caller's earlier work
     void* slot[kSlots] = {};
     const size_t slot_bytes = max_n * w;
-    std::vector<size_t> order;   // the non-empty arrays
-    for (size_t i = 0; i < count; ++i)
-        if (n[i]) order.push_back(i);
-    const int nslots = (int)std::min<size_t>(kSlots, order.size());
+    const int nslots = (int)std::min<size_t>(kSlots, count);
     for (int k = 0; k < nslots; ++k) {
         cudaError_t e = cudaMallocAsync(&slot[k], slot_bytes, s);
         if (e != cudaSuccess) {
@@ -109,24 +114,20 @@ extern "C" evosort_status evosort_sort_host_batch(const void* const* keys_in, vo
         }
     }
     cudaEventRecord(r.ev_alloc, s);
-    cudaStreamWaitEvent(r.xfer, r.ev_alloc, 0);
+    cudaStreamWaitEvent(r.up, r.ev_alloc, 0);
+    cudaStreamWaitEvent(r.down, r.ev_alloc, 0);
 
     evosort_status st = EVOSORT_OK;
-    auto upload = [&](size_t j) {
-        const size_t i = order[j];
-        const int k = (int)(j % kSlots);
-        cudaError_t e = cudaMemcpyAsync(slot[k], keys_in[i], n[i] * w, cudaMemcpyHostToDevice, r.xfer);
-        cudaEventRecord(r.loaded[k], r.xfer);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            st = fail(EVOSORT_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
-        }
-    };
-    upload(0);
-    for (size_t j = 0; j < order.size() && st == EVOSORT_OK; ++j) {
-        const size_t i = order[j];
-        const int k = (int)(j % kSlots);
-        // sort array j on the caller's stream once it is on the device
+    size_t k = 0;   // slot of the next non-empty array
+    size_t used = 0;
+    for (size_t i = 0; i < count && st == EVOSORT_OK; ++i) {
+        if (n[i] == 0) continue;
+        const size_t bytes = n[i] * w;
+        // upload into the slot once the download of its previous array is done
+        if (used >= (size_t)nslots) cudaStreamWaitEvent(r.up, r.drained[k], 0);
+        cudaError_t e = cudaMemcpyAsync(slot[k], keys_in[i], bytes, cudaMemcpyHostToDevice, r.up);
+        cudaEventRecord(r.loaded[k], r.up);
+        // sort on the caller's stream
         evosort_params pi = base;
         if (plan_each) {
             const int cls = classify_host(keys_in[i], n[i], dt);
@@ -141,22 +142,31 @@ extern "C" evosort_status evosort_sort_host_batch(const void* const* keys_in, vo
             pi.stream = base.stream;
         }
         cudaStreamWaitEvent(s, r.loaded[k], 0);
-        st = evosort_sort(slot[k], n[i], dt, &pi);
-        cudaEventRecord(r.sorted[k], s);
-        if (st != EVOSORT_OK) break;
-        // the next upload goes first (its slot's previous download is
-        // already on the copy stream), then this array's download
-        if (j + 1 < order.size()) upload(j + 1);
-        cudaStreamWaitEvent(r.xfer, r.sorted[k], 0);
-        cudaError_t e = cudaMemcpyAsync(keys_out[i], slot[k], n[i] * w, cudaMemcpyDeviceToHost, r.xfer);
-        if (e != cudaSuccess) {
+        if (e == cudaSuccess) {
+            st = evosort_sort(slot[k], n[i], dt, &pi);
+        } else {
             cudaGetLastError();
-            st = fail(EVOSORT_ERR_CUDA, std::string("download: ") + cudaGetErrorString(e));
+            st = fail(EVOSORT_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
         }
+        cudaEventRecord(r.sorted[k], s);
+        // download after the sort
+        cudaStreamWaitEvent(r.down, r.sorted[k], 0);
+        if (st == EVOSORT_OK) {
+            e = cudaMemcpyAsync(keys_out[i], slot[k], bytes, cudaMemcpyDeviceToHost, r.down);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                st = fail(EVOSORT_ERR_CUDA, std::string("download: ") + cudaGetErrorString(e));
+            }
+        }
+        cudaEventRecord(r.drained[k], r.down);
+        k = (k + 1) % nslots;
+        ++used;
     }
-    // the caller's stream waits for the copy stream, then returns the slots
-    cudaEventRecord(r.ev_xfer_done, r.xfer);
-    cudaStreamWaitEvent(s, r.ev_xfer_done, 0);
+    // the caller's stream waits for both copy streams, then returns the slots
+    cudaEventRecord(r.ev_up_done, r.up);
+    cudaEventRecord(r.ev_down_done, r.down);
+    cudaStreamWaitEvent(s, r.ev_up_done, 0);
+    cudaStreamWaitEvent(s, r.ev_down_done, 0);
     for (int j = 0; j < nslots; ++j) cudaFreeAsync(slot[j], s);
     return st;
 }
