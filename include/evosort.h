@@ -189,8 +189,8 @@ typedef enum {
     EVOSORT_CLASS_SKEWED = 1,    /* over a quarter of the keys share the top byte */
     EVOSORT_CLASS_NARROW = 2,    /* at most half of the key bits vary (more than 16) */
     EVOSORT_CLASS_FEW = 3,       /* at most 64 distinct values in the sample */
-    EVOSORT_CLASS_SORTED = 4,    /* >= 90% of sampled neighbours ascending */
-    EVOSORT_CLASS_REVERSE = 5,   /* >= 90% of sampled neighbours descending */
+    EVOSORT_CLASS_SORTED = 4,    /* >= 90% of the unequal sampled neighbours rise */
+    EVOSORT_CLASS_REVERSE = 5,   /* >= 90% of the unequal sampled neighbours fall */
     EVOSORT_CLASS_CONSTANT = 6,  /* one value */
     EVOSORT_CLASS_NARROW16 = 7   /* at most 16 key bits vary */
 } evosort_dist_class;

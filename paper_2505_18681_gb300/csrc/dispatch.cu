@@ -56,11 +56,14 @@ int classify_sample(const unsigned char* buf, size_t m, int dt) {
         std::memcpy(&u, buf + i * w, w);
         raw[i] = host_map(u, dt);
     }
-    size_t asc = 0, desc = 0;
+    // strict rises and falls between neighbours: equal neighbours say
+    // nothing about order (90% zeros would otherwise read as both sorted and
+    // reverse sorted)
+    size_t up = 0, down = 0;
     uint64_t vary = 0;
     for (size_t i = 0; i + 1 < m; ++i) {
-        asc += raw[i] <= raw[i + 1];
-        desc += raw[i] >= raw[i + 1];
+        up += raw[i] < raw[i + 1];
+        down += raw[i] > raw[i + 1];
     }
     for (size_t i = 0; i < m; ++i) vary |= raw[i] ^ raw[0];
     std::vector<uint64_t> sorted(raw);
@@ -73,9 +76,10 @@ int classify_sample(const unsigned char* buf, size_t m, int dt) {
     int bits = 0;
     while (bits < 64 && (vary >> bits)) ++bits;
     if (distinct == 1) return EVOSORT_CLASS_CONSTANT;
-    if (asc >= (size_t)(0.9 * (m - 1)) && asc > desc) return EVOSORT_CLASS_SORTED;
-    if (desc >= (size_t)(0.9 * (m - 1))) return EVOSORT_CLASS_REVERSE;
-    if (distinct <= 64) return EVOSORT_CLASS_FEW;
+    if (distinct <= 64) return EVOSORT_CLASS_FEW;          // few values, whatever their order
+    const size_t moves = up + down;
+    if (up >= 0.9 * (double)moves) return EVOSORT_CLASS_SORTED;
+    if (down >= 0.9 * (double)moves) return EVOSORT_CLASS_REVERSE;
     if (bits <= 16) return EVOSORT_CLASS_NARROW16;
     if (bits <= 4 * w) return EVOSORT_CLASS_NARROW;          // at most half the key bits vary
     if (topmax * 4 > m) return EVOSORT_CLASS_SKEWED;         // a quarter in one top byte

@@ -29,6 +29,20 @@ def test_classify_workload_distributions(evo, dist):
     assert evo.classify(x) == EXPECTED_CLASS[dist]
 
 
+def test_classify_equal_neighbours_and_order(evo):
+    """Equal neighbours do not count as order: 90% zeros is skewed, not
+    sorted or reverse; sorted keys with many repeats are still sorted; few
+    distinct values are 'few' in any order."""
+    from paper_2505_18681_gb300 import inputs
+    x = inputs.generate("paper_sparse", 1_000_003, torch.int32, seed=42, device="cuda")
+    assert evo.classify(x) == "skewed"
+    rep = torch.arange(1_000_003, device="cuda", dtype=torch.int64) // 7
+    assert evo.classify(rep) == "sorted"
+    assert evo.classify(rep.flip(0).contiguous()) == "reverse"
+    few = inputs.generate("distinct16", 1_000_003, torch.int64, seed=42, device="cuda")
+    assert evo.classify(torch.sort(few).values) == "few"
+
+
 def test_tune_small_sample_against_oracle(evo):
     """The GA with the oracle's sorted sample as the reference: every winning
     genome produced the exact answer; the log is consistent."""
