@@ -619,10 +619,41 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
             }
         }
         {
-            uint32_t tot;
-            uint32_t ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tot);
+            uint32_t ex = 0;
+            if (G > 1 && bins >= 32 && BLOCK >= 1024) {
+                // the tile counts are in s_tcnt: one warp scans them (each
+                // lane a run of bins / 32 digits) instead of a block-wide scan
+                // with its three barriers (faster with 32 warps; with 16 the
+                // block-wide scan measured faster)
+                __syncthreads();
+                if (warp == 0) {
+                    constexpr int PL = bins >= 32 ? bins / 32 : 1;
+                    uint32_t c[PL];
+                    uint32_t sum = 0;
+#pragma unroll
+                    for (int j = 0; j < PL; ++j) {
+                        c[j] = s_tcnt[lane * PL + j];
+                        sum += c[j];
+                    }
+                    uint32_t inc = sum;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    uint32_t run = inc - sum;
+#pragma unroll
+                    for (int j = 0; j < PL; ++j) {
+                        s_excl[lane * PL + j] = run;
+                        run += c[j];
+                    }
+                }
+            } else {
+                uint32_t tot;
+                ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tot);
+            }
             if (G > 1) {
-                if (tid < bins) s_excl[tid] = ex;
+                if (bins < 32 && tid < bins) s_excl[tid] = ex;
                 __syncthreads();
                 // prefixes biased by the digit's offset in the tile, so the
                 // reorder needs one lookup per key
