@@ -620,7 +620,8 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
         }
         {
             uint32_t ex = 0;
-            if (G > 1 && bins >= 32 && BLOCK >= 1024) {
+            constexpr bool kWarpScan = G > 1 && bins >= 32 && BLOCK >= 1024;
+            if (kWarpScan) {
                 // the tile counts are in s_tcnt: one warp scans them (each
                 // lane a run of bins / 32 digits) instead of a block-wide scan
                 // with its three barriers (faster with 32 warps; with 16 the
@@ -653,7 +654,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                 ex = block_exclusive_scan<BLOCK>(mysum, s_scr, &tot);
             }
             if (G > 1) {
-                if (bins < 32 && tid < bins) s_excl[tid] = ex;
+                if (!kWarpScan && tid < bins) s_excl[tid] = ex;
                 __syncthreads();
                 // prefixes biased by the digit's offset in the tile, so the
                 // reorder needs one lookup per key
