@@ -100,6 +100,9 @@ typedef struct {
     void* stream;             /* cudaStream_t */
     void* workspace;          /* optional caller scratch, device, 256-B aligned */
     size_t workspace_bytes;
+    int descending;           /* nonzero: non-increasing order (stable: equal keys,
+                                 and the values moving with them, keep their input
+                                 order); default 0, ascending */
 } evosort_params;
 
 /* Fills *p with the built-in defaults (radix, d = 8, no workspace, NULL stream). */

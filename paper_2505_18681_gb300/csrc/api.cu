@@ -202,7 +202,7 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     a.vtmp = pairs ? (uint32_t*)(base + L.off_vtmp) : nullptr;
     a.n = n;
     a.dt = dt;
-    a.map = key_map_for(dt);
+    a.map = key_map_for(dt, pl.descending);
     a.d = pl.digit_bits;
     a.npass = L.npass;
     a.lb64 = L.lb64;
@@ -276,6 +276,7 @@ static void defaults_for(int w, Plan* pl) {
     pl->insertion_threshold = 32;
     pl->rank_mode = 4;
     pl->seg_block_cap = w == 4 ? 8192 : 4096;
+    pl->descending = false;
 }
 
 // Default radix tile shape: the first of a preference list (largest tiles
@@ -305,6 +306,7 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
         default_tile_shape(w, pairs, pl);
         return EVOSORT_OK;
     }
+    pl->descending = p->descending != 0;
     if (p->algo != EVOSORT_ALGO_AUTO) pl->algo = p->algo;
     if (p->digit_bits) pl->digit_bits = p->digit_bits;
     if (p->block_size) pl->block_size = p->block_size;
@@ -392,12 +394,14 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     evosort_params planned;
     if ((!p || p->algo == EVOSORT_ALGO_AUTO) && table_nonempty()) {
         void* st = p ? p->stream : nullptr;
-        const evosort_status ps = evosort_plan(in, n, dt, st, &planned, nullptr);
+        const bool desc = p && p->descending;
+        const evosort_status ps = plan_for(in, n, dt, st, desc, &planned, nullptr);
         if (ps != EVOSORT_OK) return finish(ps, evosort_last_error());
         if (p) {
             planned.stream = p->stream;
             planned.workspace = p->workspace;
             planned.workspace_bytes = p->workspace_bytes;
+            planned.descending = p->descending;
         }
         p = &planned;
     }

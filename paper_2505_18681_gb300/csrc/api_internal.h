@@ -20,13 +20,18 @@ struct Plan {
     int insertion_threshold;  // mergesort base-run length
     int rank_mode;            // radix tile ranking variant
     int seg_block_cap;        // segmented sort: longest segment sorted in shared memory
+    bool descending;          // non-increasing order
 };
 
 void set_error(const std::string& msg);
 void default_radix_plan(int dt, Plan* pl);
 bool table_nonempty();
-int classify_sample(const unsigned char* buf, size_t m, int dt);
-int classify_host(const void* keys, size_t n, int dt);
+int classify_sample(const unsigned char* buf, size_t m, int dt, bool descending = false);
+int classify_host(const void* keys, size_t n, int dt, bool descending = false);
+// evosort_plan for a sort in the given direction (the class is read in the
+// order the sort will produce)
+evosort_status plan_for(const void* keys, size_t n, int dt, void* stream, bool descending, evosort_params* out,
+                        int* cls_out);
 bool table_lookup(int dt, size_t n, int cls, evosort_params* out);
 
 void count_launches(uint64_t k);

@@ -59,36 +59,40 @@ __device__ __forceinline__ uint64_t from_ordered(uint64_t t, int dt) {
 }
 
 // The same maps without branches, for kernels that apply them per key:
-//   forward  t = (x ^ ((sar(x) & F) | S)) - R
-//   inverse  x = u ^ ((~sar(u) & F) | S),  u = t + R
+//   forward  t = ((x ^ ((sar(x) & F) | S)) - R) ^ X
+//   inverse  x = u ^ ((~sar(u) & F) | S),  u = (t ^ X) + R
 // with (F, S, R) = (0, 0, 0) unsigned, (0, signbit, 0) signed and
 // (all-ones, signbit, 2^m - 1) float; sar is the arithmetic shift by w-1.
+// X is 0 for an ascending sort and all ones for a descending one (the
+// complement reverses the order, and equal keys stay equal, so a stable
+// ascending sort of the complemented keys is the stable descending sort).
 struct KeyMap {
-    unsigned long long f, s, r;
+    unsigned long long f, s, r, x;
 };
-inline KeyMap key_map_for(int dt) {
-    KeyMap m{0, 0, 0};
+inline KeyMap key_map_for(int dt, bool descending = false) {
+    KeyMap m{0, 0, 0, 0};
     if (dt == DT_I32) m.s = 0x80000000ull;
     if (dt == DT_I64) m.s = 0x8000000000000000ull;
-    if (dt == DT_F32) m = {0xFFFFFFFFull, 0x80000000ull, 0x007FFFFFull};
-    if (dt == DT_F64) m = {~0ull, 0x8000000000000000ull, 0x000FFFFFFFFFFFFFull};
+    if (dt == DT_F32) m = {0xFFFFFFFFull, 0x80000000ull, 0x007FFFFFull, 0};
+    if (dt == DT_F64) m = {~0ull, 0x8000000000000000ull, 0x000FFFFFFFFFFFFFull, 0};
+    if (descending) m.x = dtype_bytes(dt) == 4 ? 0xFFFFFFFFull : ~0ull;
     return m;
 }
 __device__ __forceinline__ uint32_t map_fwd(uint32_t x, const KeyMap& m) {
     const uint32_t sar = (uint32_t)((int32_t)x >> 31);
-    return (x ^ ((sar & (uint32_t)m.f) | (uint32_t)m.s)) - (uint32_t)m.r;
+    return ((x ^ ((sar & (uint32_t)m.f) | (uint32_t)m.s)) - (uint32_t)m.r) ^ (uint32_t)m.x;
 }
 __device__ __forceinline__ uint64_t map_fwd(uint64_t x, const KeyMap& m) {
     const uint64_t sar = (uint64_t)((int64_t)x >> 63);
-    return (x ^ ((sar & m.f) | m.s)) - m.r;
+    return ((x ^ ((sar & m.f) | m.s)) - m.r) ^ m.x;
 }
 __device__ __forceinline__ uint32_t map_inv(uint32_t t, const KeyMap& m) {
-    const uint32_t u = t + (uint32_t)m.r;
+    const uint32_t u = (t ^ (uint32_t)m.x) + (uint32_t)m.r;
     const uint32_t sar = (uint32_t)((int32_t)u >> 31);
     return u ^ ((~sar & (uint32_t)m.f) | (uint32_t)m.s);
 }
 __device__ __forceinline__ uint64_t map_inv(uint64_t t, const KeyMap& m) {
-    const uint64_t u = t + m.r;
+    const uint64_t u = (t ^ m.x) + m.r;
     const uint64_t sar = (uint64_t)((int64_t)u >> 63);
     return u ^ ((~sar & m.f) | m.s);
 }

@@ -31,30 +31,30 @@ std::vector<Entry> g_tab;
 
 constexpr int kSample = 4096;
 
-uint64_t host_map(uint64_t u, int dt) {
+uint64_t host_map(uint64_t u, int dt, bool descending) {
     // order-preserving map of key bits, host copy (same definition as the kernels')
     const int w = dtype_bytes(dt);
-    const KeyMap m = key_map_for(dt);
+    const KeyMap m = key_map_for(dt, descending);
     if (w == 4) {
         const uint32_t x = (uint32_t)u;
         const uint32_t sar = (x & 0x80000000u) ? 0xFFFFFFFFu : 0u;
-        return (uint32_t)((x ^ ((sar & (uint32_t)m.f) | (uint32_t)m.s)) - (uint32_t)m.r);
+        return (uint32_t)(((x ^ ((sar & (uint32_t)m.f) | (uint32_t)m.s)) - (uint32_t)m.r) ^ (uint32_t)m.x);
     }
     const uint64_t sar = (u >> 63) ? ~0ull : 0ull;
-    return (u ^ ((sar & m.f) | m.s)) - m.r;
+    return ((u ^ ((sar & m.f) | m.s)) - m.r) ^ m.x;
 }
 
 }  // namespace
 
 // Class of a sample of m keys (raw bytes, m x key width), taken at stride
-// n / m from an array of n keys.
-int classify_sample(const unsigned char* buf, size_t m, int dt) {
+// n / m from an array of n keys, read in the order of the sort's direction.
+int classify_sample(const unsigned char* buf, size_t m, int dt, bool descending) {
     const int w = dtype_bytes(dt);
     std::vector<uint64_t> raw(m, 0);
     for (size_t i = 0; i < m; ++i) {
         uint64_t u = 0;
         std::memcpy(&u, buf + i * w, w);
-        raw[i] = host_map(u, dt);
+        raw[i] = host_map(u, dt, descending);
     }
     // strict rises and falls between neighbours: equal neighbours say
     // nothing about order (90% zeros would otherwise read as both sorted and
@@ -88,14 +88,14 @@ int classify_sample(const unsigned char* buf, size_t m, int dt) {
 
 // Class of n keys in host memory, from the same strided sample the device
 // path copies (read here directly, no CUDA call).
-int classify_host(const void* keys, size_t n, int dt) {
+int classify_host(const void* keys, size_t n, int dt, bool descending) {
     if (n < 2) return EVOSORT_CLASS_CONSTANT;
     const int w = dtype_bytes(dt);
     const size_t m = n < (size_t)kSample ? n : (size_t)kSample;
     const size_t stride = n / m;
     std::vector<unsigned char> buf(m * w);
     for (size_t i = 0; i < m; ++i) std::memcpy(buf.data() + i * w, (const unsigned char*)keys + i * stride * w, w);
-    return classify_sample(buf.data(), m, dt);
+    return classify_sample(buf.data(), m, dt, descending);
 }
 
 // Table entry for (dt, n, cls): the class itself at the nearest size bucket,
@@ -124,13 +124,10 @@ bool table_nonempty() {
     return !g_tab.empty();
 }
 
-}  // namespace evosort
-
-using namespace evosort;
-
-extern "C" {
-
-evosort_status evosort_classify(const void* keys, size_t n, evosort_dtype dt, void* stream, int* cls) {
+// Class of keys[0..n) (a device array) from a strided sample, read in the
+// order of the sort's direction (synchronises the stream).
+evosort_status classify_device(const void* keys, size_t n, int dt, void* stream, bool descending,
+                                        int* cls) {
     set_error("");
     if (!cls || (n && !keys) || dt < EVOSORT_I32 || dt > EVOSORT_F64) {
         set_error("evosort_classify: bad argument");
@@ -152,8 +149,39 @@ evosort_status evosort_classify(const void* keys, size_t n, evosort_dtype dt, vo
         set_error(std::string("evosort_classify: sample copy: ") + cudaGetErrorString(e));
         return EVOSORT_ERR_CUDA;
     }
-    *cls = classify_sample(buf.data(), m, dt);
+    *cls = classify_sample(buf.data(), m, dt, descending);
     return EVOSORT_OK;
+}
+
+evosort_status plan_for(const void* keys, size_t n, int dt, void* stream, bool descending,
+                                 evosort_params* out, int* cls_out) {
+    set_error("");
+    if (!out) {
+        set_error("evosort_plan: null output");
+        return EVOSORT_ERR_INVALID;
+    }
+    evosort_default_params(out);
+    out->stream = stream;
+    int cls = EVOSORT_CLASS_RANDOM;
+    if (table_nonempty() && n >= 2) {
+        const evosort_status st = classify_device(keys, n, dt, stream, descending, &cls);
+        if (st != EVOSORT_OK) return st;
+        if (table_lookup(dt, n, cls, out)) out->stream = stream;
+        out->descending = descending ? 1 : 0;
+    }
+    if (cls_out) *cls_out = cls;
+    return EVOSORT_OK;
+}
+
+}  // namespace evosort
+
+using namespace evosort;
+
+extern "C" {
+
+
+evosort_status evosort_classify(const void* keys, size_t n, evosort_dtype dt, void* stream, int* cls) {
+    return classify_device(keys, n, dt, stream, false, cls);
 }
 
 evosort_status evosort_table_set(evosort_dtype dt, int size_bucket, int cls, const evosort_params* p, float ms) {
@@ -231,21 +259,7 @@ evosort_status evosort_table_load(const char* path) {
 
 evosort_status evosort_plan(const void* keys, size_t n, evosort_dtype dt, void* stream, evosort_params* out,
                             int* cls_out) {
-    set_error("");
-    if (!out) {
-        set_error("evosort_plan: null output");
-        return EVOSORT_ERR_INVALID;
-    }
-    evosort_default_params(out);
-    out->stream = stream;
-    int cls = EVOSORT_CLASS_RANDOM;
-    if (table_nonempty() && n >= 2) {
-        const evosort_status st = evosort_classify(keys, n, dt, stream, &cls);
-        if (st != EVOSORT_OK) return st;
-        if (table_lookup(dt, n, cls, out)) out->stream = stream;
-    }
-    if (cls_out) *cls_out = cls;
-    return EVOSORT_OK;
+    return plan_for(keys, n, dt, stream, false, out, cls_out);
 }
 
 }  // extern "C"

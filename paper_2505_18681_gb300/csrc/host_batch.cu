@@ -130,12 +130,13 @@ extern "C" evosort_status evosort_sort_host_batch(const void* const* keys_in, vo
         // sort on the caller's stream
         evosort_params pi = base;
         if (plan_each) {
-            const int cls = classify_host(keys_in[i], n[i], dt);
+            const int cls = classify_host(keys_in[i], n[i], dt, base.descending != 0);
             evosort_params tp;
             if (table_lookup(dt, n[i], cls, &tp)) {
                 pi = tp;
                 pi.workspace = base.workspace;
                 pi.workspace_bytes = base.workspace_bytes;
+                pi.descending = base.descending;
             } else {
                 pi.algo = EVOSORT_ALGO_RADIX;
             }

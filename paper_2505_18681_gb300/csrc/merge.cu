@@ -253,7 +253,7 @@ int merge_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     a.vout = vout;
     a.vtmp = pairs ? (uint32_t*)(base + (n * w + 255) / 256 * 256) : nullptr;
     a.n = n;
-    a.map = key_map_for(dt);
+    a.map = key_map_for(dt, pl.descending);
     a.tins = pl.insertion_threshold;
     int t = a.tins;
     while (t * 2 <= kMTile) t *= 2;

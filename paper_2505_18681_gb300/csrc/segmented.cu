@@ -314,7 +314,7 @@ int segmented_sort(void* keys, size_t total, const uint64_t* off, size_t nseg, i
     a.off = off;
     a.nseg = nseg;
     a.total = total;
-    a.map = key_map_for(dt);
+    a.map = key_map_for(dt, pl.descending);
     a.hdr = (uint32_t*)ws;
     a.order = (uint32_t*)((char*)ws + seg_hdr_bytes());
     a.tmp = (char*)ws + seg_hdr_bytes() + (nseg * 4 + 255) / 256 * 256;
