@@ -281,29 +281,39 @@ static void defaults_for(int w, Plan* pl) {
 
 // Default radix tile shape: the first of a preference list (largest tiles
 // first, so fewer tiles are in flight in the look-back) that fits.
-static void default_tile_shape(int w, bool pairs, Plan* pl) {
+// With n known (n > 0), a tile is skipped while it would leave more than
+// half of the SMs without a tile (n / tile < SMs / 2) and a smaller preferred
+// tile fits: small sorts then fill the GPU.  (The GA's winners at 2^20 keys
+// follow this rule: 8K-key tiles for 32-bit keys, against 16K above 2^22.)
+static void default_tile_shape(int w, bool pairs, Plan* pl, size_t n = 0) {
     static const int pref4[][2] = {{512, 32}, {1024, 16}, {512, 16}, {1024, 8}, {256, 16}, {256, 8}};
     static const int pref8[][2] = {{1024, 8}, {512, 16}, {512, 8}, {256, 16}, {256, 8}, {256, 8}};
     const int(*pref)[2] = w == 4 ? pref4 : pref8;
+    int chosen = -1;
     for (int i = 0; i < 6; ++i) {
         const int b = pl->block_size ? pl->block_size : pref[i][0];
         const int k = pl->keys_per_thread ? pl->keys_per_thread : pref[i][1];
         if (onesweep_config_fits(w, pairs, b, k, pl->digit_bits, pl->rank_mode) &&
             onesweep_rank_fits(pl->rank_mode, b, k, w, pairs, pl->digit_bits)) {
-            pl->block_size = b;
-            pl->keys_per_thread = k;
-            return;
+            chosen = i;
+            const bool fills = n == 0 || n / ((size_t)b * k) >= (size_t)(sm_count() / 2);
+            if (fills || (pl->block_size && pl->keys_per_thread)) break;
         }
+    }
+    if (chosen >= 0) {
+        if (!pl->block_size) pl->block_size = pref[chosen][0];
+        if (!pl->keys_per_thread) pl->keys_per_thread = pref[chosen][1];
+        return;
     }
     if (!pl->block_size) pl->block_size = 256;
     if (!pl->keys_per_thread) pl->keys_per_thread = 16;
 }
 
-static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::string* err) {
+static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::string* err, size_t n = 0) {
     const int w = dtype_bytes(dt);
     defaults_for(w, pl);
     if (!p) {
-        default_tile_shape(w, pairs, pl);
+        default_tile_shape(w, pairs, pl, n);
         return EVOSORT_OK;
     }
     pl->descending = p->descending != 0;
@@ -342,7 +352,7 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
         return EVOSORT_ERR_INVALID;
     }
     if (pl->algo == EVOSORT_ALGO_RADIX && (!pl->block_size || !pl->keys_per_thread))
-        default_tile_shape(dtype_bytes(dt), pairs, pl);
+        default_tile_shape(dtype_bytes(dt), pairs, pl, n);
     if (pl->algo == EVOSORT_ALGO_RADIX && !onesweep_shape_supported(pl->block_size, pl->keys_per_thread)) {
         *err = "params.block_size/keys_per_thread: unsupported radix tile shape";
         return EVOSORT_ERR_INVALID;
@@ -406,7 +416,7 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
         p = &planned;
     }
     Plan pl;
-    int rc = resolve(p, dt, pairs, &pl, &err);
+    int rc = resolve(p, dt, pairs, &pl, &err, n);
     if (rc) return finish(rc, err);
     if (pl.algo == EVOSORT_ALGO_RADIX &&
         (!onesweep_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits, pl.rank_mode) ||
@@ -457,7 +467,7 @@ size_t evosort_workspace_bytes(size_t n, evosort_dtype dt, int with_values, cons
     std::string err;
     if (!valid_dtype(dt)) return 0;
     Plan pl;
-    if (resolve(p, dt, with_values != 0, &pl, &err)) return 0;
+    if (resolve(p, dt, with_values != 0, &pl, &err, n)) return 0;
     const int w = dtype_bytes(dt);
     if (pl.algo == EVOSORT_ALGO_MERGE) return merge_workspace_bytes(n, w, with_values != 0, pl);
     return radix_workspace_bytes(n, w, with_values != 0, pl);
