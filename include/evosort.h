@@ -79,8 +79,11 @@ typedef struct {
     int algo;                 /* evosort_algo */
     int digit_bits;           /* radix digit width d, 4..11 (default 8); the
                                  paper fixes d = 8 (one byte per pass) */
-    int keys_per_thread;      /* keys each thread holds in a tile */
-    int block_size;           /* threads per CTA: 256, 512 or 1024 */
+    int keys_per_thread;      /* keys each thread holds in a tile (8, 16 or 32) */
+    int block_size;           /* threads per CTA: 256, 512 or 1024; the default
+                                 radix tile is the largest of a preference list
+                                 that fits shared memory and gives at least
+                                 half of the SMs a tile */
     int insertion_threshold;  /* mergesort base-run length T_insertion, 2..2048
                                  (default 32; Section 4.2 bounds) */
     int rank_mode;            /* radix tile ranking (how a warp finds lanes with
@@ -88,11 +91,12 @@ typedef struct {
                                  2 = one ballot per digit bit (any d),
                                  3 = shared-memory match masks (d <= 8),
                                  4 = adaptive (d = 8; default): per pass,
-                                     match masks, or match.any when the pass's
-                                     digit is concentrated (sum of squared
-                                     digit shares > 1/32) and the pass is not
-                                     the first to run; sorts below 2^21 keys
-                                     use match masks only */
+                                     match.any when the pass's digit is
+                                     concentrated (sum of squared digit
+                                     shares above 1/32, or above 1/4 for the
+                                     first pass to run), else match masks;
+                                     sorts below 2^21 keys use match masks
+                                     only */
     int seg_block_cap;        /* segmented sort: segments up to this many keys are
                                  sorted by one CTA in shared memory, longer ones by
                                  a CTA-local radix sort; 256..8192 (32-bit keys),
