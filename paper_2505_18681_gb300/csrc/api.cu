@@ -287,7 +287,7 @@ static void defaults_for(int w, Plan* pl) {
 // follow this rule: 8K-key tiles for 32-bit keys, against 16K above 2^22.)
 static void default_tile_shape(int w, bool pairs, Plan* pl, size_t n = 0) {
     static const int pref4[][2] = {{512, 32}, {1024, 16}, {512, 16}, {1024, 8}, {256, 16}, {256, 8}};
-    static const int pref8[][2] = {{1024, 8}, {512, 16}, {512, 8}, {256, 16}, {256, 8}, {256, 8}};
+    static const int pref8[][2] = {{1024, 8}, {512, 16}, {1024, 4}, {512, 8}, {256, 16}, {256, 8}};
     const int(*pref)[2] = w == 4 ? pref4 : pref8;
     int chosen = -1;
     for (int i = 0; i < 6; ++i) {

@@ -318,11 +318,17 @@ __host__ __device__ constexpr size_t onesweep_smem_vw(int block, int kpt, int w,
            ((size_t)1 << d) * 20 + ((2 << d) <= block ? ((size_t)1 << d) * 16 : 0) + 16;
 }
 // two virtual warps per warp where their counters fit, else one
-__host__ __device__ constexpr int onesweep_vw(int block, int kpt, int w, bool pairs, int d) {
-    return (kpt % 2 == 0 && onesweep_smem_vw(block, kpt, w, pairs, d, 2) <= kMaxDynSmem) ? 2 : 1;
+// (Rank mode 3, and 4 which launches it, also needs the match masks of the
+// virtual warps, one 32-bit word per digit each, to fit in the reorder buffer.)
+__host__ __device__ constexpr int onesweep_vw(int block, int kpt, int w, bool pairs, int d, int rank = 0) {
+    return (kpt % 2 == 0 && onesweep_smem_vw(block, kpt, w, pairs, d, 2) <= kMaxDynSmem &&
+            ((rank != 3 && rank != 4) ||
+             (size_t)(block / 32) * 2 * ((size_t)1 << d) * 4 <= (size_t)block * kpt * w))
+               ? 2
+               : 1;
 }
 __host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int w, bool pairs, int d, int rank) {
-    return onesweep_smem_vw(block, kpt, w, pairs, d, onesweep_vw(block, kpt, w, pairs, d));
+    return onesweep_smem_vw(block, kpt, w, pairs, d, onesweep_vw(block, kpt, w, pairs, d, rank));
 }
 
 // Decoupled look-back for one digit: sums the counts of the preceding tiles
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     unsigned char* bufs = smem;   // two input tile buffers of KB + VB bytes
     U* s_rkeys = (U*)(smem + 2 * (KB + VB));                  // reorder buffer
     uint32_t* s_rvals = (uint32_t*)(smem + 2 * (KB + VB) + KB);
-    constexpr int kVW = onesweep_vw(BLOCK, KPT, (int)sizeof(U), PAIRS, D);
+    constexpr int kVW = onesweep_vw(BLOCK, KPT, (int)sizeof(U), PAIRS, D, RANK);
     constexpr int NVW = WARPS * kVW;   // virtual warps, in input order
     uint16_t* s_whist = (uint16_t*)(smem + 3 * (KB + VB));
     uint32_t* s_excl = (uint32_t*)(s_whist + NVW * bins);
@@ -788,7 +794,7 @@ __global__ void __launch_bounds__(256) radix_fixup(RadixArgs a) {
 namespace evosort {
 // The rank-3 match masks must fit in the reorder buffer.
 constexpr bool match_masks_fit(int block, int kpt, int w, bool pairs, int d) {
-    return (size_t)(block / 32) * onesweep_vw(block, kpt, w, pairs, d) * ((size_t)1 << d) * 4 <=
+    return (size_t)(block / 32) * onesweep_vw(block, kpt, w, pairs, d, 3) * ((size_t)1 << d) * 4 <=
            (size_t)block * kpt * w;
 }
 }  // namespace evosort

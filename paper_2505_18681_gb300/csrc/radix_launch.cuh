@@ -10,6 +10,7 @@ namespace evosort {
 #define EVOSORT_TILE_SHAPES(X) \
     X(256, 8)                  \
     X(256, 16)                 \
+    X(1024, 4)                 \
     X(512, 8)                  \
     X(512, 16)                 \
     X(512, 32)                 \

@@ -103,7 +103,7 @@ def tile_fits(block, kpt, w, pairs, d, rank):
     counters (two virtual warps per warp), digit offsets, counts, partial sums
     and bases, two mbarriers (<= 227 KB less 1 KB).
     Rank mode 3 keeps its match masks in the reorder buffer."""
-    return smem_vw(block, kpt, w, pairs, d, vw_of(block, kpt, w, pairs, d)) <= LIMIT
+    return smem_vw(block, kpt, w, pairs, d, vw_of(block, kpt, w, pairs, d, rank)) <= LIMIT
 
 
 LIMIT = 232448 - 1024
@@ -116,12 +116,15 @@ def smem_vw(block, kpt, w, pairs, d, vw):
     return s
 
 
-def vw_of(block, kpt, w, pairs, d):
-    """Two virtual warps per warp where their counters fit, else one."""
-    return 2 if kpt % 2 == 0 and smem_vw(block, kpt, w, pairs, d, 2) <= LIMIT else 1
+def vw_of(block, kpt, w, pairs, d, rank=0):
+    """Two virtual warps per warp where their counters (and, for match-mask
+    ranking, their masks in the reorder buffer) fit, else one."""
+    masks_ok = rank not in (3, 4) or block // 32 * 2 * (1 << d) * 4 <= block * kpt * w
+    return 2 if kpt % 2 == 0 and smem_vw(block, kpt, w, pairs, d, 2) <= LIMIT and masks_ok else 1
 
 
-@pytest.mark.parametrize("shape", [(256, 8), (256, 16), (512, 8), (512, 16), (512, 32), (1024, 8), (1024, 16)])
+@pytest.mark.parametrize("shape", [(256, 8), (256, 16), (1024, 4), (512, 8), (512, 16), (512, 32), (1024, 8),
+                                   (1024, 16)])
 @pytest.mark.parametrize("rank", [1, 2, 3, 4])
 @pytest.mark.parametrize("d", [6, 8, 11])
 def test_tile_shapes_and_ranking(evo, shape, rank, d):
@@ -137,7 +140,7 @@ def test_tile_shapes_and_ranking(evo, shape, rank, d):
             runner = run_pairs if pairs else run_keys
             compiled = rank == 2 or (rank in (1, 4) and d == 8) or (rank == 3 and d <= 8)
             masks_fit = rank not in (3, 4) or \
-                block // 32 * vw_of(block, kpt, w, pairs, d) * (1 << d) * 4 <= block * kpt * w
+                block // 32 * vw_of(block, kpt, w, pairs, d, 3) * (1 << d) * 4 <= block * kpt * w
             if compiled and masks_fit and tile_fits(block, kpt, w, pairs, d, rank):
                 runner(evo, x, **kw)
             else:
