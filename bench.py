@@ -13,7 +13,7 @@ match-mask ranking, default tile: no per-class or per-pass choice), and
 "defaults", the library's defaults (adaptive per-pass ranking).  With
 --params plain only the fixed-parameter arm runs.
 
-JSON line fields follow the driver contract: value (whole-job GKeys/s),
+JSON line fields: value (whole-job GKeys/s),
 ms_per_step, e2e (same metric through the C ABI with pinned host buffers and
 the copies inside the timed region), roofline (dominant kernel, algorithmic
 bytes / CUDA-event time vs measured HBM copy bandwidth), cpu_baseline (the CPU

@@ -64,7 +64,7 @@ typedef enum {
     EVOSORT_ERR_NOMEM = 2,       /* device memory or caller workspace too small */
     EVOSORT_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     EVOSORT_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
-    EVOSORT_ERR_UNSUPPORTED = 5  /* valid request this build cannot serve */
+    EVOSORT_ERR_UNSUPPORTED = 5  /* valid request the library cannot serve */
 } evosort_status;
 
 /* Algorithm choice, the A_code gene of Section 4.2 (3 = mergesort, 4 = radix). */
@@ -154,7 +154,7 @@ evosort_status evosort_sort_pairs_to(const void* keys_in, const uint32_t* values
  * later work on p->stream waits for all of it: evosort_sync(p->stream) or a
  * stream synchronisation makes the host outputs ready.  Host buffers should
  * be page-locked (cudaHostAlloc / cudaHostRegister): pageable buffers are
- * still sorted correctly, but the driver then stages each copy and the
+ * still sorted correctly, but the CUDA driver then stages each copy and the
  * overlap is lost.  n[i] == 0 arrays are skipped.  Errors before anything is
  * enqueued (bad arguments, no device memory) return a status; a failure of a
  * later array's sort returns its status with the earlier arrays' work left

@@ -45,7 +45,7 @@ const DevInfo* device_info(std::string* err) {
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&di.status, g_status_word);
         if (e == cudaSuccess) {
             // keep freed scratch in the stream-ordered pool instead of returning
-            // it to the driver after every call
+            // it to the CUDA driver after every call
             cudaMemPool_t pool;
             if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
                 uint64_t thr = ~0ull;

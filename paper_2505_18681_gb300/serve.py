@@ -3,7 +3,7 @@
 Requests carry host (pinned) keys of int32, int64 or float64.  The loop:
 
 * admits waiting requests in arrival order while the device has room for
-  them: free HBM (driver-free plus what PyTorch's allocator holds unused),
+  them: free HBM (free as the CUDA driver reports it, plus what PyTorch's allocator holds unused),
   less a reserve, less what admitted but unfinished requests have reserved;
 * whenever one of its CUDA streams is idle, launches work on it: all admitted
   small requests of the oldest waiting dtype, packed into one batched

@@ -5,7 +5,7 @@ seeded sample of a representative workload of that class, on the GPU, and
 the winning parameters go into the table under (dtype, floor(log2 n), class).
 Candidates are verified on the device (sortedness and a multiset fingerprint
 of the input); no CPU code takes part.  The paper tunes per array size with a
-population of 30 over 10 generations (Section 4.2); so does this driver, per
+population of 30 over 10 generations (Section 4.2); so does this script, per
 class as well.
 
     python -m paper_2505_18681_gb300.tune --dtype int64 --n 268435456 \\
