@@ -309,3 +309,24 @@ def test_paper_distributions_int32(evo, dist):
         run_keys(evo, x)
     finally:
         evo.table_clear()
+
+
+@pytest.mark.parametrize("algo", ["radix", "merge"])
+def test_cuda_graph_capture_of_a_device_wide_sort(evo, algo):
+    """A whole sort (histogram, plan, passes, fixup, stream-ordered scratch)
+    is captured once and replayed on new keys in the same buffers."""
+    n = 2_500_003
+    x = gen("uniform", n, torch.int64, seed=1)
+    y = torch.empty_like(x)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        evo.sort(x, out=y, algo=algo, stream=s)     # warm-up outside capture (device set-up)
+        evo.sync(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            evo.sort(x, out=y, algo=algo, stream=s)
+    for seed in (2, 3):
+        x.copy_(gen("gaussian", n, torch.int64, seed=seed))
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(bits(y), oracle.radix_sort(x.cpu().numpy()).view(np.uint64))
