@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--kpt", type=int, default=0)
     ap.add_argument("--rank-mode", type=int, default=0)
+    ap.add_argument("--pass-kernel", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=1 << 23, help="keys per distribution for the oracle")
     ap.add_argument("--sizes", default="1e7,1e8,1e9,5e9", help="paper9 workload: array sizes")
     ap.add_argument("--workload", default="nine",
@@ -297,6 +298,8 @@ def main():
         kw["keys_per_thread"] = args.kpt
     if args.rank_mode:
         kw["rank_mode"] = args.rank_mode
+    if args.pass_kernel:
+        kw["pass_kernel"] = args.pass_kernel
     stream = torch.cuda.current_stream()
     # plain: one sort call per array with fixed parameters (8-bit digits,
     # match-mask ranking, the default tile), no per-class or per-pass choice

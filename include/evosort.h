@@ -107,6 +107,14 @@ typedef struct {
     int descending;           /* nonzero: non-increasing order (stable: equal keys,
                                  and the values moving with them, keep their input
                                  order); default 0, ascending */
+    int pass_kernel;          /* radix pass kernel: 0 = default, 1 = staged tile
+                                 (the tile is copied into shared memory by the
+                                 TMA engine, then ranked), 2 = register tile (keys
+                                 loaded into registers, ranked one column of 32 at
+                                 a time), 3 = register tile with two independent
+                                 ranking chains per warp; 2 and 3 exist for 32-bit
+                                 keys-only sorts with 8-bit digits and rank modes
+                                 1-4 */
 } evosort_params;
 
 /* Fills *p with the built-in defaults (radix, d = 8, no workspace, NULL stream). */

@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
                 ("block_size", ctypes.c_int), ("insertion_threshold", ctypes.c_int),
                 ("rank_mode", ctypes.c_int), ("seg_block_cap", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t), ("descending", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_size_t), ("descending", ctypes.c_int), ("pass_kernel", ctypes.c_int)]
 
 
 class GAConfig(ctypes.Structure):
@@ -183,7 +183,7 @@ def _stream_handle(stream) -> int:
 
 def make_params(algo=None, digit_bits=0, keys_per_thread=0, block_size=0, insertion_threshold=0,
                 rank_mode=0, seg_block_cap=0, stream=None, workspace: torch.Tensor | None = None,
-                descending=False) -> Params:
+                descending=False, pass_kernel=0) -> Params:
     p = Params()
     library().evosort_default_params(ctypes.byref(p))
     p.algo = ALGOS[algo]
@@ -194,6 +194,7 @@ def make_params(algo=None, digit_bits=0, keys_per_thread=0, block_size=0, insert
     p.rank_mode = int(rank_mode or 0)
     p.seg_block_cap = int(seg_block_cap or 0)
     p.descending = 1 if descending else 0
+    p.pass_kernel = int(pass_kernel or 0)
     p.stream = _stream_handle(stream)
     if workspace is not None:
         p.workspace = workspace.data_ptr()

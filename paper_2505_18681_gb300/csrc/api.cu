@@ -236,11 +236,16 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
         ProfScope ps(call, EVOSORT_K_RADIX_SCAN, -1, 0.0, 0, s);
         if (e == cudaSuccess) e = launch_radix_aux(w, 1, 1, 0, s, a, inplace);
     }
+    const bool reg = pl.pass_kernel == 2;
     for (int p = 0; p < L.npass && e == cudaSuccess; ++p) {
         for (int v = 0; v < (adapt ? 2 : 1) && e == cudaSuccess; ++v) {
             const int r = v == 0 ? rank : 1;
             ProfScope ps(call, EVOSORT_K_RADIX_ONESWEEP, p, pass_bytes, n, s, adapt ? r : 0);
-            if (w == 4)
+            if (reg && w == 4)
+                e = launch_onesweep_reg_u32(pairs, pl.block_size, pl.keys_per_thread, r, L.ntiles, sms, s, a, p);
+            else if (reg)
+                e = launch_onesweep_reg_u64(pairs, pl.block_size, pl.keys_per_thread, r, L.ntiles, sms, s, a, p);
+            else if (w == 4)
                 e = launch_onesweep_u32(pairs, pl.block_size, pl.keys_per_thread, r, L.ntiles, sms, s, a, p);
             else
                 e = launch_onesweep_u64(pairs, pl.block_size, pl.keys_per_thread, r, L.ntiles, sms, s, a, p);
@@ -277,15 +282,64 @@ static void defaults_for(int w, Plan* pl) {
     pl->rank_mode = 4;
     pl->seg_block_cap = w == 4 ? 8192 : 4096;
     pl->descending = false;
+    pl->pass_kernel = 0;   // chosen with the tile shape
 }
 
-// Default radix tile shape: the first of a preference list (largest tiles
-// first, so fewer tiles are in flight in the look-back) that fits.
-// With n known (n > 0), a tile is skipped while it would leave more than
-// half of the SMs without a tile (n / tile < SMs / 2) and a smaller preferred
-// tile fits: small sorts then fill the GPU.  (The GA's winners at 2^20 keys
-// follow this rule: 8K-key tiles for 32-bit keys, against 16K above 2^22.)
+// Register-tile shapes in order of preference per key width and form, and
+// whether the register tile is the default pass kernel for that form (where
+// it measured faster than the staged tile).
+static const int kRegPref32k[][2] = {{1024, 16}, {512, 16}};
+static const int kRegPref32p[][2] = {{1024, 12}, {1024, 8}};
+static const int kRegPref64k[][2] = {{1024, 12}, {1024, 8}, {512, 8}};
+static const int kRegPref64p[][2] = {{1024, 12}, {1024, 8}, {512, 8}};
+
+// Measured at 1e9 int64 / 5e8 key-value sorts: 5.30 vs 6.54 ms per int64 pass,
+// 29.9 vs 43.9 ms for float64 + uint32 pairs, 12.3 vs 14.4 ms for int32 pairs.
+static bool reg_by_default(int, bool) { return true; }
+
+static void reg_prefs(int w, bool pairs, const int (**pref)[2], int* np) {
+    if (w == 4 && !pairs) { *pref = kRegPref32k; *np = 2; }
+    else if (w == 4) { *pref = kRegPref32p; *np = 2; }
+    else if (!pairs) { *pref = kRegPref64k; *np = 3; }
+    else { *pref = kRegPref64p; *np = 3; }
+}
+
+// Default radix tile shape and pass kernel.  The register tile is tried first
+// when it is requested (pass_kernel 2) or is the default for the form
+// (pass_kernel 0); the staged tile otherwise, or when no register tile gives
+// at least half of the SMs a tile of a small input.  Within a kernel the
+// first shape of the preference list (largest tiles first, so fewer tiles
+// are in flight in the look-back) that fits is taken; with n known (n > 0), a
+// shape is skipped while it would leave more than half of the SMs without a
+// tile (n / tile < SMs / 2) and a smaller preferred shape fits: small sorts
+// then fill the GPU.  (The GA's winners at 2^20 keys follow this rule: 8K-key
+// tiles for 32-bit keys, against 16K above 2^22.)
 static void default_tile_shape(int w, bool pairs, Plan* pl, size_t n = 0) {
+    const bool given = pl->block_size && pl->keys_per_thread;
+    const size_t half = (size_t)(sm_count() / 2);
+    if (pl->pass_kernel == 2 || (pl->pass_kernel == 0 && reg_by_default(w, pairs))) {
+        const int(*pref)[2];
+        int np = 0;
+        reg_prefs(w, pairs, &pref, &np);
+        int chosen = -1;
+        for (int i = 0; i < np; ++i) {
+            const int b = pl->block_size ? pl->block_size : pref[i][0];
+            const int k = pl->keys_per_thread ? pl->keys_per_thread : pref[i][1];
+            if (!reg_config_fits(w, pairs, b, k, pl->digit_bits, pl->rank_mode)) continue;
+            chosen = i;
+            if (given || n == 0 || n / ((size_t)b * k) >= half) break;
+            chosen = -2 - i;   // fits, but leaves SMs idle: keep looking
+        }
+        if (chosen >= 0 || (pl->pass_kernel == 2 && chosen != -1)) {
+            const int i = chosen >= 0 ? chosen : -2 - chosen;
+            if (!pl->block_size) pl->block_size = pref[i][0];
+            if (!pl->keys_per_thread) pl->keys_per_thread = pref[i][1];
+            pl->pass_kernel = 2;
+            return;
+        }
+        if (pl->pass_kernel == 2) return;   // nothing fits: reported by the caller's check
+    }
+    pl->pass_kernel = 1;
     static const int pref4[][2] = {{512, 32}, {1024, 16}, {512, 16}, {1024, 8}, {256, 16}, {256, 8}};
     static const int pref8[][2] = {{1024, 8}, {512, 16}, {1024, 4}, {512, 8}, {256, 16}, {256, 8}};
     const int(*pref)[2] = w == 4 ? pref4 : pref8;
@@ -296,8 +350,8 @@ static void default_tile_shape(int w, bool pairs, Plan* pl, size_t n = 0) {
         if (onesweep_config_fits(w, pairs, b, k, pl->digit_bits, pl->rank_mode) &&
             onesweep_rank_fits(pl->rank_mode, b, k, w, pairs, pl->digit_bits)) {
             chosen = i;
-            const bool fills = n == 0 || n / ((size_t)b * k) >= (size_t)(sm_count() / 2);
-            if (fills || (pl->block_size && pl->keys_per_thread)) break;
+            const bool fills = n == 0 || n / ((size_t)b * k) >= half;
+            if (fills || given) break;
         }
     }
     if (chosen >= 0) {
@@ -327,6 +381,11 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
         *err = "params.seg_block_cap must be in [256, 8192] (32-bit keys) or [256, 4096] (64-bit keys)";
         return EVOSORT_ERR_INVALID;
     }
+    pl->pass_kernel = p->pass_kernel;
+    if (pl->pass_kernel < 0 || pl->pass_kernel > 2) {
+        *err = "params.pass_kernel must be 0, 1 or 2";
+        return EVOSORT_ERR_INVALID;
+    }
     if (p->rank_mode) pl->rank_mode = p->rank_mode;
     else if (pl->digit_bits > 8) pl->rank_mode = 2;   // match masks are compiled for d <= 8
     else if (pl->digit_bits < 8) pl->rank_mode = 3;   // match.any is compiled for d = 8
@@ -351,9 +410,10 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
                "digit_bits <= 8";
         return EVOSORT_ERR_INVALID;
     }
-    if (pl->algo == EVOSORT_ALGO_RADIX && (!pl->block_size || !pl->keys_per_thread))
+    if (pl->algo == EVOSORT_ALGO_RADIX && (!pl->block_size || !pl->keys_per_thread || !pl->pass_kernel))
         default_tile_shape(dtype_bytes(dt), pairs, pl, n);
-    if (pl->algo == EVOSORT_ALGO_RADIX && !onesweep_shape_supported(pl->block_size, pl->keys_per_thread)) {
+    if (pl->algo == EVOSORT_ALGO_RADIX && pl->pass_kernel != 2 &&
+        !onesweep_shape_supported(pl->block_size, pl->keys_per_thread)) {
         *err = "params.block_size/keys_per_thread: unsupported radix tile shape";
         return EVOSORT_ERR_INVALID;
     }
@@ -418,7 +478,11 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     Plan pl;
     int rc = resolve(p, dt, pairs, &pl, &err, n);
     if (rc) return finish(rc, err);
-    if (pl.algo == EVOSORT_ALGO_RADIX &&
+    if (pl.algo == EVOSORT_ALGO_RADIX && pl.pass_kernel == 2 &&
+        !reg_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits, pl.rank_mode))
+        return finish(EVOSORT_ERR_INVALID, "register-tile radix pass (pass_kernel 2): needs 8-bit digits, rank mode "
+                                           "1, 3 or 4 and a compiled tile shape for this key width");
+    if (pl.algo == EVOSORT_ALGO_RADIX && pl.pass_kernel != 2 &&
         (!onesweep_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits, pl.rank_mode) ||
          !onesweep_rank_fits(pl.rank_mode, pl.block_size, pl.keys_per_thread, w, pairs, pl.digit_bits)))
         return finish(EVOSORT_ERR_INVALID, "radix tile does not fit in shared memory (block_size x "
@@ -512,6 +576,7 @@ evosort_status evosort_segmented_sort(void* keys, size_t total, const uint64_t* 
     if (total && !keys) return finish(EVOSORT_ERR_INVALID, "null key pointer");
     if ((uintptr_t)keys % w) return finish(EVOSORT_ERR_INVALID, "misaligned key pointer");
     if (nseg >= 0xFFFFFFFFull) return finish(EVOSORT_ERR_UNSUPPORTED, "nseg >= 2^32");
+    if (total >= (1ull << 40)) return finish(EVOSORT_ERR_UNSUPPORTED, "total >= 2^40");
     Plan pl;
     int rc = resolve(p, dt, false, &pl, &err);
     if (rc) return finish(rc, err);

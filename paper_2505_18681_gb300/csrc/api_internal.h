@@ -21,6 +21,7 @@ struct Plan {
     int rank_mode;            // radix tile ranking variant
     int seg_block_cap;        // segmented sort: longest segment sorted in shared memory
     bool descending;          // non-increasing order
+    int pass_kernel;          // radix pass kernel: 1 staged tile, 2/3 register tile (1/2 chains per warp)
 };
 
 void set_error(const std::string& msg);

@@ -114,6 +114,34 @@ cudaError_t launch_onesweep_u64_keys(int block, int kpt, int rank, size_t grid, 
                                      const RadixArgs& a, int pass);
 cudaError_t launch_onesweep_u64_pairs(int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
                                       const RadixArgs& a, int pass);
+// Register-tile pass kernels (onesweep_reg.cuh): (threads per CTA, keys per
+// thread) compiled per key width and form, 8-bit digits, rank modes 1, 3, 4.
+#define EVOSORT_REG_SHAPES_U32_KEYS(X) X(1024, 16) X(512, 16)
+#define EVOSORT_REG_SHAPES_U32_PAIRS(X) X(1024, 12) X(1024, 8)
+#define EVOSORT_REG_SHAPES_U64_KEYS(X) X(1024, 12) X(1024, 8) X(512, 8)
+#define EVOSORT_REG_SHAPES_U64_PAIRS(X) X(1024, 12) X(1024, 8) X(512, 8)
+
+// Defined in radix32r.cu and radix64r.cu.
+cudaError_t launch_onesweep_reg_u32(bool pairs, int block, int kpt, int rank, size_t grid, int sms,
+                                    cudaStream_t s, const RadixArgs& a, int pass);
+cudaError_t launch_onesweep_reg_u64(bool pairs, int block, int kpt, int rank, size_t grid, int sms,
+                                    cudaStream_t s, const RadixArgs& a, int pass);
+
+// True if the register tile of this shape is compiled for the key width and
+// form and supports the digit width and rank mode.
+inline bool reg_config_fits(int w, bool pairs, int block, int kpt, int d, int rank) {
+    if (d != 8 || (rank != 1 && rank != 3 && rank != 4)) return false;
+    bool shape = false;
+#define EVOSORT_CASE(B, K) \
+    if (block == B && kpt == K) shape = true;
+    if (w == 4 && !pairs) { EVOSORT_REG_SHAPES_U32_KEYS(EVOSORT_CASE) }
+    if (w == 4 && pairs) { EVOSORT_REG_SHAPES_U32_PAIRS(EVOSORT_CASE) }
+    if (w == 8 && !pairs) { EVOSORT_REG_SHAPES_U64_KEYS(EVOSORT_CASE) }
+    if (w == 8 && pairs) { EVOSORT_REG_SHAPES_U64_PAIRS(EVOSORT_CASE) }
+#undef EVOSORT_CASE
+    return shape;
+}
+
 // Defined in radix_aux.cu.
 cudaError_t launch_onesweep_u32(bool pairs, int block, int kpt, int rank, size_t grid, int sms, cudaStream_t s,
                                 const RadixArgs& a, int pass);

@@ -47,13 +47,21 @@ struct SegArgs {
 
 __device__ __forceinline__ int len_bucket(uint64_t len) { return 63 - __clzll((long long)len); }
 
+// A segment is sorted only if it lies inside the array: lo <= hi <= total.
+// Any other segment is reported (ST_BAD_OFFSETS) and left out of the work
+// list, so no tier ever reads or writes outside [0, total).  total < 2^40 is
+// checked on the host, so a valid length always has a bucket below kNB.
+__device__ __forceinline__ bool seg_ok(const SegArgs& a, uint64_t lo, uint64_t hi) {
+    return lo <= hi && hi <= a.total;
+}
+
 // K7a: validate offsets, count segments per length bucket.
 __global__ void seg_count(SegArgs a) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && (a.off[0] != 0 || a.off[a.nseg] != a.total)) atomicOr(a.status, ST_BAD_OFFSETS);
     if (i >= a.nseg) return;
     const uint64_t lo = a.off[i], hi = a.off[i + 1];
-    if (hi < lo) {
+    if (!seg_ok(a, lo, hi)) {
         atomicOr(a.status, ST_BAD_OFFSETS);
         return;
     }
@@ -83,7 +91,7 @@ __global__ void seg_fill(SegArgs a) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.nseg) return;
     const uint64_t lo = a.off[i], hi = a.off[i + 1];
-    if (hi < lo || hi - lo < 2) return;
+    if (!seg_ok(a, lo, hi) || hi - lo < 2) return;
     const uint32_t p = atomicAdd(&a.hdr[kNB + len_bucket(hi - lo)], 1u);
     a.order[p] = (uint32_t)i;
 }

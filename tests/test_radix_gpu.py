@@ -128,11 +128,11 @@ def vw_of(block, kpt, w, pairs, d, rank=0):
 @pytest.mark.parametrize("rank", [1, 2, 3, 4])
 @pytest.mark.parametrize("d", [6, 8, 11])
 def test_tile_shapes_and_ranking(evo, shape, rank, d):
-    """Every compiled tile shape and ranking variant; shapes whose tile does
-    not fit in shared memory, match.any ranking at a width other than 8 bits
-    and match-mask ranking above 8 bits must be rejected with ERR_INVALID."""
+    """Every compiled staged-tile shape and ranking variant; shapes whose tile
+    does not fit in shared memory, match.any ranking at a width other than 8
+    bits and match-mask ranking above 8 bits must be rejected with ERR_INVALID."""
     block, kpt = shape
-    kw = dict(algo="radix", block_size=block, keys_per_thread=kpt, rank_mode=rank, digit_bits=d)
+    kw = dict(algo="radix", block_size=block, keys_per_thread=kpt, rank_mode=rank, digit_bits=d, pass_kernel=1)
     for dtype in (torch.uint32, torch.int64):
         w = 4 if dtype == torch.uint32 else 8
         x = gen("zipf" if dtype == torch.int64 else "uniform", 150_011, dtype)
@@ -147,6 +147,52 @@ def test_tile_shapes_and_ranking(evo, shape, rank, d):
                 with pytest.raises(evo.EvoSortError) as ei:
                     runner(evo, x, **kw)
                 assert ei.value.status == "ERR_INVALID"
+
+
+REG_SHAPES = {(4, False): [(1024, 16), (512, 16)], (4, True): [(1024, 12), (1024, 8)],
+              (8, False): [(1024, 12), (1024, 8), (512, 8)], (8, True): [(1024, 12), (1024, 8), (512, 8)]}
+
+
+@pytest.mark.parametrize("dtype", ALL, ids=str)
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+def test_register_tile_shapes(evo, dtype, pairs):
+    """Every compiled register-tile shape (pass_kernel 2) with match masks,
+    match.any and adaptive ranking, at sizes around one tile, several tiles
+    with a ragged tail, in place and out of place, against the oracle."""
+    w = torch.empty(0, dtype=dtype).element_size()
+    runner = run_pairs if pairs else run_keys
+    for block, kpt in REG_SHAPES[(w, pairs)]:
+        tile = block * kpt
+        for n in (1, tile - 1, tile + 1, 5 * tile + 37):
+            x = gen("float_mix" if dtype.is_floating_point else "gaussian", n, dtype, seed=n % 97)
+            for rank in (1, 3, 4):
+                runner(evo, x, algo="radix", pass_kernel=2, block_size=block, keys_per_thread=kpt, rank_mode=rank)
+            runner(evo, x, inplace=True, algo="radix", pass_kernel=2, block_size=block, keys_per_thread=kpt)
+
+
+def test_register_tile_rejections(evo):
+    """The register tile exists for 8-bit digits and rank modes 1, 3 and 4:
+    other requests for it are rejected, and pass_kernel outside 0..2 too."""
+    x = gen("uniform", 10_000, torch.int32)
+    for kw in (dict(digit_bits=6), dict(rank_mode=2), dict(block_size=256, keys_per_thread=8)):
+        with pytest.raises(evo.EvoSortError) as ei:
+            run_keys(evo, x, algo="radix", pass_kernel=2, **kw)
+        assert ei.value.status == "ERR_INVALID"
+    with pytest.raises(evo.EvoSortError) as ei:
+        run_keys(evo, x, algo="radix", pass_kernel=3)
+    assert ei.value.status == "ERR_INVALID"
+
+
+@pytest.mark.parametrize("dist", ["uniform", "gaussian", "distinct16", "sorted"])
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64], ids=str)
+def test_staged_and_register_tiles_agree_with_oracle(evo, dist, dtype):
+    """Both pass kernels at their default shapes on the same input, each
+    against the oracle (the default picks the register tile)."""
+    x = gen(dist, ADAPT_N, dtype, seed=21)
+    run_keys(evo, x, algo="radix", pass_kernel=1)
+    run_keys(evo, x, algo="radix", pass_kernel=2)
+    run_pairs(evo, x, algo="radix", pass_kernel=1)
+    run_pairs(evo, x, algo="radix", pass_kernel=2)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=str)

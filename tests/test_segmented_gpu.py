@@ -105,6 +105,18 @@ def test_bad_offsets_reported(evo):
     with pytest.raises(evo.EvoSortError):
         evo.sync()
     evo.sync()   # the status word is cleared after it is reported
+    # a segment that ends past the array: reported, and left untouched (the
+    # check skips it before any tier reads or writes its keys)
+    guard = torch.arange(300, dtype=torch.int32, device="cuda").flip(0)
+    keys = guard[:100]
+    before = guard.clone()
+    offs = torch.tensor([0, 200, 100], dtype=torch.int64, device="cuda")
+    evo.segmented_sort(keys, offs)
+    with pytest.raises(evo.EvoSortError) as ei:
+        evo.sync()
+    assert ei.value.status == "ERR_INVALID"
+    assert torch.equal(guard[100:], before[100:]), "keys past the array were touched"
+    evo.sync()
 
 
 def test_cuda_graph_capture_and_replay(evo):
