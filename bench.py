@@ -1,25 +1,36 @@
 #!/usr/bin/env python3
 """Benchmark: GKeys/s of the GB300 sort path on the nine-distribution 1e9-key
-int64 workload, with the HBM roofline of its dominant kernel.
+int64 workload, with the HBM roofline of its dominant kernel, and the other
+configurations measured beside it.
 
-One step = one sort of each of the nine seeded 1e9-key int64 arrays (uniform,
-Gaussian, sorted, reverse, nearly sorted, 16 distinct, Zipf, all-equal,
-uniform [0, 1000)), each read from its own resident input buffer and written
-to an output buffer (inputs are 8 GB each, far larger than L2, so no flush is
-needed between steps).  Each array is sorted with the parameters of the tuned
-table for its sampled distribution class ("tuned", the headline value).  Two
-more arms sort the same arrays: "plain", fixed parameters (8-bit digits,
-match-mask ranking, default tile: no per-class or per-pass choice), and
-"defaults", the library's defaults (adaptive per-pass ranking).  With
---params plain only the fixed-parameter arm runs.
+Headline step (value): one sort of each of the nine seeded 1e9-key int64
+arrays (uniform, Gaussian, sorted, reverse, nearly sorted, 16 distinct, Zipf,
+all-equal, uniform [0, 1000)), each read from its own resident input buffer
+and written to an output buffer (inputs are 8 GB each, far larger than L2, so
+no flush is needed between steps).  Each sort is the call a user makes with
+the choice left to the library: the dispatcher samples the array, classifies
+it and takes the GA-tuned table's parameters ("tuned").  Two more arms sort
+the same arrays: "plain", fixed parameters (8-bit digits, match-mask ranking,
+the default tile: no per-class or per-pass choice), and "defaults", the
+library's built-in parameters.
 
-JSON line fields: value (whole-job GKeys/s),
-ms_per_step, e2e (same metric through the C ABI with pinned host buffers and
-the copies inside the timed region), roofline (dominant kernel, algorithmic
-bytes / CUDA-event time vs measured HBM copy bandwidth), cpu_baseline (the CPU
-oracle on a bounded sample), clocks, gpu_launches.
+The other configurations run after the headline (single GPU only) and are
+reported as sub-objects of the same JSON line: "int32" (the same nine
+distributions as 1e9-key int32 arrays, with its own roofline), "floatpairs"
+(5e8 float64 keys with a uint32 index, stable), "segmented" (100,000 int32
+arrays of log-uniform length 16..1e6, one batched call, tuned vs defaults vs
+one call per array), "u32big" (1e10 uint32 keys in one sort), "small" (latency
+of 1e3..1e4-key sorts through the one-CTA path against the radix path) and
+"merge" (mergesort of 1e8 int32 keys).
+
+JSON line fields: value (whole-job GKeys/s), ms_per_step, e2e (same metric
+through the C ABI with pinned host buffers and the copies inside the timed
+region), roofline (dominant kernel, algorithmic bytes / CUDA-event time vs
+measured HBM copy bandwidth), cpu_baseline (the CPU oracle on a bounded
+sample), clocks, gpu_launches, and the sub-objects above.
 
     python bench.py                       # N=1, defaults
+    python bench.py --no-extras           # the headline only
     python bench.py --impl reference      # the CPU oracle arm
     torchrun --nproc-per-node N bench.py --gpus N   # N replicas, weak scaling
 """
@@ -53,6 +64,7 @@ def parse():
     ap.add_argument("--dtype", default="int64", choices=["int32", "int64", "uint32", "uint64"])
     ap.add_argument("--dists", default=",".join(DISTS))
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="measure the headline configuration only")
     ap.add_argument("--cpu-par-sample", type=int, default=1 << 24,
                     help="keys per distribution for the multithreaded CPU baseline")
     ap.add_argument("--no-cpu", action="store_true")
@@ -65,7 +77,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1 << 23, help="keys per distribution for the oracle")
     ap.add_argument("--sizes", default="1e7,1e8,1e9,5e9", help="paper9 workload: array sizes")
     ap.add_argument("--workload", default="nine",
-                    choices=["nine", "floatpairs", "segmented", "u32big", "paper9", "friendster"],
+                    choices=["nine", "int32", "floatpairs", "segmented", "u32big", "small", "merge", "paper9",
+                             "friendster"],
                     help="nine: the headline workload; the others measure the other configurations")
     ap.add_argument("--segments", type=int, default=100_000)
     return ap.parse_args()
@@ -104,29 +117,9 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_from_profiles(kernel_src_hash: str):
-    """DRAM bytes per key per pass of the onesweep kernel from the committed
-    ncu summary, or None if the summary is absent or the kernel has changed."""
-    p = os.path.join(ROOT, "profiles", "radix_onesweep_traffic.txt")
-    if not os.path.exists(p):
-        return None
-    vals = {}
-    with open(p) as f:
-        for line in f:
-            if "=" in line and not line.startswith("#"):
-                k, v = line.strip().split("=", 1)
-                vals[k.strip()] = v.strip()
-    if vals.get("kernel_sha256") != kernel_src_hash:
-        return None
-    try:
-        return float(vals["dram_bytes_per_key_per_pass"])
-    except (KeyError, ValueError):
-        return None
-
-
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("radix.cuh", "common.cuh"):
+    for f in ("onesweep_reg.cuh", "radix.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2505_18681_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -256,6 +249,176 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 # GPU arm.
 # ---------------------------------------------------------------------------
+TABLE_DIR = os.path.join(ROOT, "paper_2505_18681_gb300", "tuned")
+
+
+def traffic_per_key_pass(w: int):
+    """DRAM bytes per key per pass of the register-tile onesweep kernel for
+    key width w, from the committed ncu summary of that width, or None if the
+    summary is absent or the kernel source has changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "radix_onesweep_reg_int%d.txt" % (8 * w))
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_sha256") != kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_key_per_pass"])
+    except (KeyError, ValueError):
+        return None
+
+
+def onesweep_roofline(recs, w, peak, peak_src):
+    """Roofline of the dominant kernel (the onesweep pass) over the active
+    launches of a timed region: algorithmic bytes / CUDA-event time."""
+    act = [r for r in recs if r["kind"] == "radix_onesweep" and r["active"]]
+    ach = (sum(r["bytes"] for r in act) / 1e9) / (sum(r["ms"] for r in act) * 1e-3) if act else 0.0
+    tpk = traffic_per_key_pass(w)
+    traffic = tpk * act[0]["items"] if (tpk is not None and act) else None
+    return {"bound": "hbm", "kernel": "radix_onesweep", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak if peak else None, "traffic": traffic, "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": act[0]["bytes"] if act else None,
+            "avg_active_launch_ms": (sum(r["ms"] for r in act) / len(act)) if act else None,
+            "active_launches": len(act)}
+
+
+def kernel_shares(recs):
+    by_kind = {}
+    for r in recs:
+        by_kind[r["kind"]] = by_kind.get(r["kind"], 0.0) + r["ms"]
+    tot = max(sum(by_kind.values()), 1e-9)
+    return {k: round(v / tot, 4) for k, v in by_kind.items()}
+
+
+def time_region(fn, steps, stream):
+    """Device time of `steps` calls of fn between two events on `stream`, and
+    the per-step times (one event per step boundary)."""
+    import torch
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for k in range(steps):
+        fn()
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(steps))
+    return evs[0].elapsed_time(evs[-1]), per
+
+
+def nine_leg(evo, args, dtype_name, n, dists, stream, rank, ws, barrier, dev, keep_inputs=False):
+    """The nine-distribution step for one key type: tuned (dispatcher call),
+    plain and defaults arms, per-distribution times, roofline of the dominant
+    kernel, kernel shares and clocks.  Returns (fields, inputs or None)."""
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    tdt = getattr(torch, dtype_name)
+    w = torch.empty(0, dtype=tdt).element_size()
+    xs = [inputs.generate(d, n, tdt, seed=42 + 1000 * rank, device=dev) for d in dists]
+    out = torch.empty(n, dtype=tdt, device=dev)
+    torch.cuda.synchronize()
+    kw = {}
+    for k, a in (("digit_bits", args.digit_bits), ("block_size", args.block), ("keys_per_thread", args.kpt),
+                 ("rank_mode", args.rank_mode), ("pass_kernel", args.pass_kernel)):
+        if a:
+            kw[k] = a
+    # plain: one sort call per array with fixed parameters (8-bit digits,
+    # match-mask ranking, the default tile), no per-class or per-pass choice
+    fixed = {"digit_bits": 8, "rank_mode": 3}
+    fixed.update(kw)
+    plain = evo.make_params(algo="radix", stream=stream, **fixed)
+    defaults = evo.make_params(algo="radix", stream=stream, **kw)
+    table = os.path.join(TABLE_DIR, "gb300_%s.txt" % dtype_name)
+    evo.table_clear()
+    mode = "plain"
+    tuned = plain
+    plans = {}
+    if args.params in ("auto", "tuned") and not kw and os.path.exists(table):
+        # the call a user makes: AUTO parameters, so the dispatcher samples
+        # each array, classifies it and takes the tuned table's entry
+        evo.table_load(table)
+        tuned = evo.make_params(stream=stream)
+        mode = "tuned"
+        for d, x in zip(dists, xs):
+            pd, cls = evo.plan(x, stream=stream)
+            plans[d] = {"class": cls, **pd}
+    elif args.params == "tuned":
+        raise SystemExit("no tuned table at %s" % table)
+
+    def step(p):
+        for x in xs:
+            evo.sort(x, out=out, params=p)
+
+    for _ in range(max(args.warmup, 0)):
+        step(tuned)
+    evo.sync(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    launches0 = evo.kernel_launches()
+    evo.profile(True)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    ms, per_step = time_region(lambda: step(tuned), args.steps, stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = evo.kernel_launches() - launches0
+    recs = evo.profile_read()
+    evo.profile(False)
+    evo.sync(stream)
+    ms_step = max_over_ranks(ms / args.steps, dev)
+    keys_per_step = n * len(dists) * ws
+
+    def time_arm(p):
+        for _ in range(max(args.warmup, 1)):
+            step(p)
+        barrier()
+        torch.cuda.synchronize()
+        t, _ = time_region(lambda: step(p), args.steps, stream)
+        return max_over_ranks(t / args.steps, dev)
+
+    plain_line = defaults_line = None
+    if mode == "tuned":
+        pms = time_arm(plain)
+        plain_line = {"value": keys_per_step / (pms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": pms,
+                      "tuned_over_plain": pms / ms_step,
+                      "params": "fixed: 8-bit digits, match-mask ranking, default tile"}
+        dms = time_arm(defaults)
+        defaults_line = {"value": keys_per_step / (dms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": dms,
+                         "tuned_over_defaults": dms / ms_step,
+                         "params": "library defaults: 8-bit digits, register tile, adaptive per-pass ranking"}
+    peak, peak_src = measured_peaks()
+    per_dist = {}
+    for d, x in zip(dists, xs):
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        evo.sort(x, out=out, params=tuned)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        per_dist[d] = round(f0.elapsed_time(f1), 3)
+    fields = {
+        "value": whole_job_gkeys(n * len(dists), ws, ms_step), "ms_per_step": ms_step,
+        "step_ms": {"min": per_step[0], "median": statistics.median(per_step), "max": per_step[-1]},
+        "config": {"workload": "nine-distribution %s sort, %d keys per array (one step sorts all nine)"
+                   % (dtype_name, n), "n_per_array": n, "dists": dists, "params": mode,
+                   "param_overrides": kw, "tuned_plans": plans,
+                   "l2": "inputs larger than L2 (%.1f GB per array), no flush" % (n * w / 1e9)},
+        "plain": plain_line, "defaults": defaults_line,
+        "roofline": onesweep_roofline(recs, w, peak, peak_src),
+        "whole_step_alg_gbs": sum(r["bytes"] for r in recs) / args.steps / 1e9 / (ms_step * 1e-3),
+        "kernel_time_share": kernel_shares(recs), "per_dist_ms": per_dist, "clocks": clocks,
+        "gpu_launches": launches, "_tuned_params": tuned,
+    }
+    if keep_inputs:
+        return fields, (xs, out)
+    del xs, out
+    return fields, None
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -277,157 +440,32 @@ def main():
             tdist.barrier()
 
     import paper_2505_18681_gb300 as evo
-    from paper_2505_18681_gb300 import inputs
     evo.library()
     dev = torch.device("cuda", local)
-    tdt = getattr(torch, args.dtype)
     dists = args.dists.split(",")
-    n = args.n
-    w = torch.empty(0, dtype=tdt).element_size()
-
-    xs = [inputs.generate(d, n, tdt, seed=42 + 1000 * rank, device=dev) for d in dists]
-    out = torch.empty(n, dtype=tdt, device=dev)
-    torch.cuda.synchronize()
-
-    kw = {}
-    if args.digit_bits:
-        kw["digit_bits"] = args.digit_bits
-    if args.block:
-        kw["block_size"] = args.block
-    if args.kpt:
-        kw["keys_per_thread"] = args.kpt
-    if args.rank_mode:
-        kw["rank_mode"] = args.rank_mode
-    if args.pass_kernel:
-        kw["pass_kernel"] = args.pass_kernel
     stream = torch.cuda.current_stream()
-    # plain: one sort call per array with fixed parameters (8-bit digits,
-    # match-mask ranking, the default tile), no per-class or per-pass choice
-    fixed = {"digit_bits": 8, "rank_mode": 3}
-    fixed.update(kw)
-    plain = [evo.make_params(algo="radix", stream=stream, **fixed) for _ in dists]
-    # the library's defaults (adaptive per-pass ranking), reported beside it
-    defaults = [evo.make_params(algo="radix", stream=stream, **kw) for _ in dists]
-    params = plain
-    mode = "plain"
-    table = os.path.join(ROOT, "paper_2505_18681_gb300", "tuned", "gb300_%s.txt" % args.dtype)
-    plans = {}
-    if args.params in ("auto", "tuned") and not kw and os.path.exists(table):
-        # GA-tuned parameters per array, chosen by the dispatcher from each
-        # array's sampled distribution class (classified once, before timing)
-        evo.table_clear()
-        evo.table_load(table)
-        params = []
-        for d, x in zip(dists, xs):
-            pd, cls = evo.plan(x, stream=stream)
-            plans[d] = {"class": cls, **pd}
-            params.append(evo.make_params(stream=stream, **pd))
-        mode = "tuned"
-    elif args.params == "tuned":
-        raise SystemExit("no tuned table at %s" % table)
-    # pre-size the scratch pool so the timed region allocates nothing new
-    ws_bytes = max(evo.workspace_bytes(n, tdt, **kw), 1)
-    pre = torch.empty(0)
-    del pre
-
-    def step(ps):
-        for x, p in zip(xs, ps):
-            evo.sort(x, out=out, params=p)
-
-    for _ in range(max(args.warmup, 0)):
-        step(params)
-    evo.sync(stream)
-    torch.cuda.synchronize()
-
-    sampler = ClockSampler(local)
-    launches0 = evo.kernel_launches()
-    evo.profile(True)
-    sampler.start()
-    barrier()
-    torch.cuda.synchronize()
-    # one event per step boundary: the K-step total and each step's time
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    evs[0].record(stream)
-    for k in range(args.steps):
-        step(params)
-        evs[k + 1].record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    e0, e1 = evs[0], evs[-1]
-    per_step = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
-    launches = evo.kernel_launches() - launches0
-    recs = evo.profile_read()
-    evo.profile(False)
-    evo.sync(stream)
-    ms = e0.elapsed_time(e1)
-    ms_step = max_over_ranks(ms / args.steps, dev)
-    keys_per_step = n * len(dists) * ws
-    value = whole_job_gkeys(n * len(dists), ws, ms_step)
-
-    # the plain arm (fixed parameters, one sort call per array) and the
-    # library-defaults arm on the same inputs, for the tuned-vs-plain comparison
-    def time_arm(ps):
-        for _ in range(max(args.warmup, 1)):
-            step(ps)
-        barrier()
-        torch.cuda.synchronize()
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        for _ in range(args.steps):
-            step(ps)
-        p1.record(stream)
-        torch.cuda.synchronize()
-        return max_over_ranks(p0.elapsed_time(p1) / args.steps, dev)
-
-    plain_line = defaults_line = None
-    if mode == "tuned":
-        pms = time_arm(plain)
-        plain_line = {"value": keys_per_step / (pms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": pms,
-                      "tuned_over_plain": pms / ms_step,
-                      "params": "fixed: 8-bit digits, match-mask ranking, default tile"}
-        dms = time_arm(defaults)
-        defaults_line = {"value": keys_per_step / (dms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": dms,
-                         "tuned_over_defaults": dms / ms_step,
-                         "params": "library defaults: 8-bit digits, adaptive per-pass ranking, default tile"}
-
-    # dominant kernel: the onesweep pass; time-weighted over active launches
-    by_kind = {}
-    for r in recs:
-        k = by_kind.setdefault(r["kind"], {"ms": 0.0, "bytes": 0.0, "launches": 0, "active": 0})
-        k["ms"] += r["ms"]
-        k["bytes"] += r["bytes"]
-        k["launches"] += 1
-        k["active"] += int(r["active"])
-    ones = by_kind.get("radix_onesweep", {"ms": 0.0, "bytes": 0.0, "active": 0, "launches": 0})
-    act = [r for r in recs if r["kind"] == "radix_onesweep" and r["active"]]
-    ach = (sum(r["bytes"] for r in act) / 1e9) / (sum(r["ms"] for r in act) * 1e-3) if act else 0.0
-    peak, peak_src = measured_peaks()
-    # the committed capture is of the 64-bit keys-only kernel; other key
-    # widths have no measured traffic
-    tpk = traffic_from_profiles(kernel_hash()) if w == 8 else None
-    traffic = None
-    if tpk is not None and act:
-        traffic = tpk * act[0]["items"]
-    total_alg = sum(r["bytes"] for r in recs)
-    shares = {k: round(v["ms"] / max(sum(x["ms"] for x in by_kind.values()), 1e-9), 4) for k, v in by_kind.items()}
-
-    # per-distribution device time of one sort each (diagnostic, after the timed region)
-    per_dist = {}
-    for d, x, p in zip(dists, xs, params):
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        evo.sort(x, out=out, params=p)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        per_dist[d] = round(f0.elapsed_time(f1), 3)
+    head, kept = nine_leg(evo, args, args.dtype, args.n, dists, stream, rank, ws, barrier, dev, keep_inputs=True)
+    xs, out = kept
+    w = xs[0].element_size()
 
     # end to end: pinned host input -> device, sort, device -> pinned host output
     e2e = None
-    if not args.no_e2e and rank == 0 or (not args.no_e2e and ws > 1):
-        e2e = measure_e2e(evo, xs, out, params, stream, n, w, args, barrier, ws, dev, mode == "tuned")
+    if not args.no_e2e:
+        e2e = measure_e2e(evo, xs, out, [head["_tuned_params"]] * len(xs), stream, args.n, w, args, barrier, ws,
+                          dev, head["config"]["params"] == "tuned")
+    del xs, out, kept
+    torch.cuda.empty_cache()
+
+    extras = {}
+    if ws == 1 and not args.no_extras:
+        for name, fn in (("int32", leg_int32), ("floatpairs", leg_floatpairs), ("segmented", leg_segmented),
+                         ("u32big", leg_u32big), ("small", leg_small), ("merge", leg_merge)):
+            try:
+                extras[name] = fn(evo, args, stream, barrier, dev)
+            except Exception as exc:   # one configuration's failure does not drop the line
+                extras[name] = {"error": "%s: %s" % (type(exc).__name__, str(exc)[:300])}
+            torch.cuda.empty_cache()
+        evo.table_clear()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -445,32 +483,18 @@ def main():
                            % (args.cpu_par_sample, len(dists))}
 
     if rank == 0:
+        cfg = head["config"]
+        cfg["parallelism"] = "replicas" if ws > 1 else "single GPU"
         line = {
-            "metric": METRIC, "value": value, "unit": "GKeys/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "step_ms": {"min": per_step[0], "median": statistics.median(per_step), "max": per_step[-1]},
-            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": "nine-distribution %s sort, %d keys per array (one step sorts all nine)"
-                       % (args.dtype, n), "n_per_array": n, "dists": dists, "params": mode,
-                       "param_overrides": kw,
-                       "tuned_plans": plans,
-                       "l2": "inputs larger than L2 (%.1f GB per array), no flush" % (n * w / 1e9),
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "e2e": e2e,
-            "plain": plain_line,
-            "defaults": defaults_line,
-            "roofline": {"bound": "hbm", "kernel": "radix_onesweep", "achieved": ach, "peak": peak,
-                         "unit": "GB/s", "frac": ach / peak if peak else None, "traffic": traffic,
-                         "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": act[0]["bytes"] if act else None,
-                         "avg_active_launch_ms": (sum(r["ms"] for r in act) / len(act)) if act else None},
-            "whole_step_alg_gbs": total_alg / args.steps / 1e9 / (ms_step * 1e-3),
-            "kernel_time_share": shares,
-            "per_dist_ms": per_dist,
-            "cpu_baseline": cpu,
-            "clocks": clocks,
-            "gpu_launches": launches,
+            "metric": METRIC, "value": head["value"], "unit": "GKeys/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "step_ms": head["step_ms"], "vs_baseline": None, "dtype": args.dtype,
+            "data": "synthetic", "config": cfg, "e2e": e2e, "plain": head["plain"], "defaults": head["defaults"],
+            "roofline": head["roofline"], "whole_step_alg_gbs": head["whole_step_alg_gbs"],
+            "kernel_time_share": head["kernel_time_share"], "per_dist_ms": head["per_dist_ms"],
+            "cpu_baseline": cpu, "clocks": head["clocks"], "gpu_launches": head["gpu_launches"],
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if ws > 1:
         tdist.destroy_process_group()
@@ -516,6 +540,188 @@ def measure_e2e(evo, xs, out, params, stream, n, w, args, barrier, ws, dev, auto
 
 
 # ---------------------------------------------------------------------------
+# The other configurations, measured after the headline on one GPU.
+# ---------------------------------------------------------------------------
+def leg_int32(evo, args, stream, barrier, dev):
+    """The nine distributions as 1e9-key int32 arrays (the configuration the
+    60%-of-HBM target is set on), with its own roofline."""
+    fields, _ = nine_leg(evo, args, "int32", args.n, args.dists.split(","), stream, 0, 1, barrier, dev)
+    fields.pop("_tuned_params", None)
+    return fields
+
+
+def _timed_with_profile(evo, fn, steps, warmup, stream):
+    import torch
+    for _ in range(max(warmup, 1)):
+        fn()
+    evo.sync(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    launches0 = evo.kernel_launches()
+    evo.profile(True)
+    sampler.start()
+    ms, _ = time_region(fn, steps, stream)
+    clocks = sampler.stop()
+    recs = evo.profile_read()
+    evo.profile(False)
+    evo.sync(stream)
+    return ms / steps, recs, clocks, evo.kernel_launches() - launches0
+
+
+def leg_floatpairs(evo, args, stream, barrier, dev):
+    """5e8 float64 keys (uniform [-1e6, 1e6], 1% duplicates, -0.0/+0.0/NaN
+    sprinkled) with a uint32 index payload: the stable argsort."""
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    n = 500_000_000
+    x = inputs.generate("float_mix", n, torch.float64, seed=42, device=dev)
+    v = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32).view(torch.uint32)
+    ko, vo = torch.empty_like(x), torch.empty_like(v)
+    p = evo.make_params(stream=stream)
+    ms, recs, clocks, launches = _timed_with_profile(evo, lambda: evo.sort_pairs(x, v, ko, vo, params=p),
+                                                     args.steps, args.warmup, stream)
+    peak, src = measured_peaks()
+    roof = onesweep_roofline(recs, 8, peak, src)
+    roof["kernel"] = "radix_onesweep (key/value)"
+    roof["traffic"] = None
+    return {"value": n / (ms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": ms, "dtype": "f64+u32",
+            "config": {"workload": "stable key/value argsort, %d float64 keys with uint32 index payload" % n},
+            "roofline": roof, "kernel_time_share": kernel_shares(recs), "clocks": clocks,
+            "gpu_launches": launches}
+
+
+def leg_segmented(evo, args, stream, barrier, dev, nseg=100_000):
+    """100,000 int32 arrays with log-uniform lengths 16..1e6 (half uniform,
+    half nearly sorted): one batched call with the GA-tuned cut-overs against
+    the built-in ones and against one sort call per array."""
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    lens = inputs.segment_lengths(nseg, 16, 1_000_000, seed=42)
+    keys, offs = inputs.segmented_keys(lens, torch.int32, seed=42, device=dev)
+    d_offs = offs.to(dev)
+    total = keys.numel()
+    work = torch.empty_like(keys)
+    evo.table_clear()
+    evo.table_load(os.path.join(TABLE_DIR, "gb300_int32.txt"))
+    tuned = evo.make_params(stream=stream)                 # AUTO: the table's segmented entry
+    defaults = evo.make_params(algo="radix", stream=stream)
+    copy_ms = _time_steps(lambda: work.copy_(keys), args.steps, 1, stream)
+
+    def batched(p):
+        def f():
+            work.copy_(keys)
+            evo.segmented_sort(work, d_offs, params=p)
+        return f
+    ms_t, recs, clocks, launches = _timed_with_profile(evo, batched(tuned), args.steps, args.warmup, stream)
+    ms_t -= copy_ms
+    ms_d = _time_steps(batched(defaults), args.steps, 1, stream) - copy_ms
+    # one sort call per array with the library's own choice (no table: the
+    # one-CTA path for short arrays, the device-wide radix sort for the rest)
+    evo.table_clear()
+    bounds = offs.tolist()
+    plain_p = evo.make_params(stream=stream)
+
+    def per_array():
+        work.copy_(keys)
+        for i in range(len(bounds) - 1):
+            a, b = bounds[i], bounds[i + 1]
+            if b - a > 1:
+                evo.sort(work[a:b], params=plain_p)
+    plain_ms = _time_steps(per_array, 1, 1, stream) - copy_ms
+    evo.sync()
+    return {"value": total / (ms_t * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": ms_t, "dtype": "i32",
+            "config": {"workload": "batched segmented sort: %d int32 arrays, log-uniform lengths 16..1e6, %d keys "
+                       "total, even arrays uniform, odd nearly sorted" % (nseg, total),
+                       "tuned_params": "GA table entry for segmented batches (class 'segmented')"},
+            "defaults": {"value": total / (ms_d * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": ms_d,
+                         "tuned_over_defaults": ms_d / ms_t},
+            "plain": {"value": total / (plain_ms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": plain_ms,
+                      "batched_over_plain": plain_ms / ms_t, "calls": len(bounds) - 1,
+                      "params": "one sort call per array, library defaults"},
+            "kernel_time_share": kernel_shares(recs), "clocks": clocks, "gpu_launches_per_batch": launches /
+            max(args.steps, 1)}
+
+
+def leg_u32big(evo, args, stream, barrier, dev):
+    """1e10 uint32 keys uniform (40 GB, double-buffered in HBM), one sort."""
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    n = 10_000_000_000
+    x = inputs.generate("uniform", n, torch.uint32, seed=42, device=dev)
+    y = torch.empty_like(x)
+    p = evo.make_params(stream=stream)
+    ms, recs, clocks, launches = _timed_with_profile(evo, lambda: evo.sort(x, out=y, params=p),
+                                                     max(1, min(args.steps, 3)), 1, stream)
+    peak, src = measured_peaks()
+    roof = onesweep_roofline(recs, 4, peak, src)
+    roof["traffic"] = None   # 64-bit look-back slots at this size: not the captured kernel configuration
+    return {"value": n / (ms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": ms, "dtype": "u32",
+            "config": {"workload": "%d uint32 keys uniform (%.0f GB, double-buffered in HBM), one sort"
+                       % (n, n * 4 / 1e9)},
+            "roofline": roof, "kernel_time_share": kernel_shares(recs), "clocks": clocks,
+            "gpu_launches": launches}
+
+
+def leg_small(evo, args, stream, barrier, dev):
+    """Latency of small sorts: the dispatcher's one-CTA path (the default for
+    arrays up to 4096 keys) against the device-wide radix path, per call."""
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    res = {}
+    for n in (1000, 4096, 10_000):
+        x = inputs.generate("uniform", n, torch.int32, seed=42, device=dev)
+        y = torch.empty_like(x)
+        row = {}
+        for label, p in (("auto", evo.make_params(stream=stream)),
+                         ("radix", evo.make_params(algo="radix", stream=stream))):
+            for _ in range(20):
+                evo.sort(x, out=y, params=p)
+            torch.cuda.synchronize()
+            dev_us, host_us = [], []
+            k0 = evo.kernel_launches()
+            for _ in range(101):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                t0 = time.perf_counter()
+                e0.record(stream)
+                evo.sort(x, out=y, params=p)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                host_us.append((time.perf_counter() - t0) * 1e6)
+                dev_us.append(e0.elapsed_time(e1) * 1e3)
+            row[label] = {"device_us_median": statistics.median(dev_us), "host_us_median": statistics.median(host_us),
+                          "launches_per_call": (evo.kernel_launches() - k0) / 101}
+        res[str(n)] = row
+    return {"unit": "us per sort", "config": {"workload": "one int32 array of 1e3 / 4096 / 1e4 uniform keys per call; "
+                                              "'auto' lets the dispatcher choose (one-CTA path up to 4096 keys), "
+                                              "'radix' forces the device-wide radix sort"},
+            "latency": res}
+
+
+def leg_merge(evo, args, stream, barrier, dev):
+    """Mergesort (Algorithm 3) of 1e8 int32 keys, insertion threshold 32:
+    GKeys/s and the achieved bandwidth of its merge rounds."""
+    import torch
+    from paper_2505_18681_gb300 import inputs
+    n = 100_000_000
+    x = inputs.generate("uniform", n, torch.int32, seed=42, device=dev)
+    y = torch.empty_like(x)
+    p = evo.make_params(algo="merge", insertion_threshold=32, stream=stream)
+    ms, recs, clocks, launches = _timed_with_profile(evo, lambda: evo.sort(x, out=y, params=p),
+                                                     max(1, min(args.steps, 3)), 1, stream)
+    passes = [r for r in recs if r["kind"] == "merge_pass"]
+    ach = sum(r["bytes"] for r in passes) / 1e9 / (sum(r["ms"] for r in passes) * 1e-3) if passes else 0.0
+    peak, src = measured_peaks()
+    steps = max(1, min(args.steps, 3))
+    return {"value": n / (ms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": ms, "dtype": "i32",
+            "config": {"workload": "mergesort of %d uniform int32 keys, insertion threshold 32" % n},
+            "roofline": {"bound": "hbm", "kernel": "merge_pass", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak if peak else None, "traffic": None, "peak_source": src,
+                         "rounds_per_sort": len(passes) // steps},
+            "kernel_time_share": kernel_shares(recs), "clocks": clocks, "gpu_launches": launches}
+
+
+# ---------------------------------------------------------------------------
 # The other configurations (one JSON line each; not the headline bench line).
 # ---------------------------------------------------------------------------
 def _time_steps(fn, steps, warmup, stream):
@@ -544,28 +750,13 @@ def other_workload(args):
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     line = {"metric": METRIC, "unit": "GKeys/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
-    if args.workload == "floatpairs":
-        n = 500_000_000 if args.n == 1_000_000_000 else args.n
-        x = inputs.generate("float_mix", n, torch.float64, seed=42, device="cuda")
-        v = torch.arange(n, dtype=torch.int64, device="cuda").to(torch.int32).view(torch.uint32)
-        ko, vo = torch.empty_like(x), torch.empty_like(v)
-        p = evo.make_params(algo="radix", stream=stream)
-        launches0 = evo.kernel_launches()
-        evo.profile(True)
-        sampler.start()
-        ms = _time_steps(lambda: evo.sort_pairs(x, v, ko, vo, params=p), args.steps, args.warmup, stream)
-        clocks = sampler.stop()
-        recs = [r for r in evo.profile_read() if r["kind"] == "radix_onesweep" and r["active"]]
-        evo.profile(False)
-        evo.sync()
-        ach = sum(r["bytes"] for r in recs) / 1e9 / (sum(r["ms"] for r in recs) * 1e-3) if recs else 0.0
-        line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="f64+u32",
-                    config={"workload": "stable key/value argsort, %d float64 keys (uniform [-1e6,1e6], 1%% "
-                            "duplicates, -0.0/+0.0/NaN sprinkled) with uint32 index payload" % n},
-                    roofline={"bound": "hbm", "kernel": "radix_onesweep (pairs)", "achieved": ach, "peak": peak,
-                              "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src},
-                    clocks=clocks, gpu_launches=evo.kernel_launches() - launches0)
-    elif args.workload == "paper9":
+    if args.workload in ("floatpairs", "segmented", "u32big", "small", "merge", "int32"):
+        leg = {"floatpairs": leg_floatpairs, "segmented": lambda *a: leg_segmented(*a, nseg=args.segments),
+               "u32big": leg_u32big, "small": leg_small, "merge": leg_merge, "int32": leg_int32}[args.workload]
+        line.update(leg(evo, args, stream, lambda: None, torch.device("cuda")))
+        print(json.dumps(line), flush=True)
+        return
+    if args.workload == "paper9":
         # the paper's nine int32 distributions over a size sweep, five timed
         # sorts each (the paper's protocol: min / median / max of 5), tuned
         # int32 table through the dispatcher
@@ -639,73 +830,6 @@ def other_workload(args):
                     roofline={"bound": "hbm", "kernel": "radix_onesweep", "achieved": ach, "peak": peak,
                               "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src},
                     clocks=clocks, gpu_launches=evo.kernel_launches() - launches0)
-    elif args.workload == "u32big":
-        n = 10_000_000_000 if args.n == 1_000_000_000 else args.n
-        x = inputs.generate("uniform", n, torch.uint32, seed=42, device="cuda")
-        y = torch.empty_like(x)
-        p = evo.make_params(algo="radix", stream=stream)
-        launches0 = evo.kernel_launches()
-        evo.profile(True)
-        sampler.start()
-        ms = _time_steps(lambda: evo.sort(x, out=y, params=p), args.steps, args.warmup, stream)
-        clocks = sampler.stop()
-        recs = [r for r in evo.profile_read() if r["kind"] == "radix_onesweep" and r["active"]]
-        evo.profile(False)
-        evo.sync()
-        ach = sum(r["bytes"] for r in recs) / 1e9 / (sum(r["ms"] for r in recs) * 1e-3) if recs else 0.0
-        line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="u32",
-                    config={"workload": "%d uint32 keys uniform (%.0f GB, double-buffered in HBM), one sort"
-                            % (n, n * 4 / 1e9)},
-                    roofline={"bound": "hbm", "kernel": "radix_onesweep", "achieved": ach, "peak": peak,
-                              "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_src},
-                    clocks=clocks, gpu_launches=evo.kernel_launches() - launches0)
-    else:   # segmented
-        lens = inputs.segment_lengths(args.segments, 16, 1_000_000, seed=42)
-        keys, offs = inputs.segmented_keys(lens, torch.int32, seed=42, device="cuda")
-        d_offs = offs.to("cuda")
-        total = keys.numel()
-        work = torch.empty_like(keys)
-        # tier threshold chosen by timing every allowed value (the batched path's only knob)
-        best_cap, best_ms = None, None
-        for cap in (1024, 2048, 4096, 8192):
-            p = evo.make_params(seg_block_cap=cap, stream=stream)
-
-            def run_batched(p=p):
-                work.copy_(keys)
-                evo.segmented_sort(work, d_offs, params=p)
-            t = _time_steps(run_batched, 1, 1, stream)
-            if best_ms is None or t < best_ms:
-                best_cap, best_ms = cap, t
-        p = evo.make_params(seg_block_cap=best_cap, stream=stream)
-        copy_ms = _time_steps(lambda: work.copy_(keys), args.steps, 1, stream)
-
-        def run_batched():
-            work.copy_(keys)
-            evo.segmented_sort(work, d_offs, params=p)
-        launches0 = evo.kernel_launches()
-        sampler.start()
-        ms = _time_steps(run_batched, args.steps, args.warmup, stream) - copy_ms
-        clocks = sampler.stop()
-        batched_launches = (evo.kernel_launches() - launches0) // (args.steps + args.warmup)
-        # plain path: one default sort call per array
-        bounds = offs.tolist()
-        plain_p = evo.make_params(algo="radix", stream=stream)
-
-        def run_plain():
-            work.copy_(keys)
-            for i in range(len(bounds) - 1):
-                a, b = bounds[i], bounds[i + 1]
-                if b - a > 1:
-                    evo.sort(work[a:b], params=plain_p)
-        plain_ms = _time_steps(run_plain, 1, 1, stream) - copy_ms
-        evo.sync()
-        line.update(value=total / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="i32",
-                    config={"workload": "batched segmented sort: %d int32 arrays, log-uniform lengths 16..1e6, "
-                            "%d keys total, even arrays uniform, odd nearly sorted" % (args.segments, total),
-                            "seg_block_cap": best_cap, "launches_per_batched_sort": batched_launches},
-                    plain={"value": total / (plain_ms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": plain_ms,
-                           "batched_over_plain": plain_ms / ms, "calls": len(bounds) - 1},
-                    clocks=clocks)
     print(json.dumps(line), flush=True)
 
 

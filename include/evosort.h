@@ -107,14 +107,37 @@ typedef struct {
     int descending;           /* nonzero: non-increasing order (stable: equal keys,
                                  and the values moving with them, keep their input
                                  order); default 0, ascending */
-    int pass_kernel;          /* radix pass kernel: 0 = default, 1 = staged tile
-                                 (the tile is copied into shared memory by the
-                                 TMA engine, then ranked), 2 = register tile (keys
-                                 loaded into registers, ranked one column of 32 at
-                                 a time), 3 = register tile with two independent
-                                 ranking chains per warp; 2 and 3 exist for 32-bit
-                                 keys-only sorts with 8-bit digits and rank modes
-                                 1-4 */
+    int pass_kernel;          /* radix pass kernel: 0 = default (the register tile
+                                 where it is compiled for the request, else the
+                                 staged tile), 1 = staged tile (the tile is copied
+                                 into shared memory by the TMA engine and ranked
+                                 there), 2 = register tile (keys loaded into
+                                 registers and ranked one column of 32 at a time;
+                                 8-bit digits, rank modes 1, 3 and 4) */
+    int adapt_later;          /* adaptive ranking (rank mode 4): a pass after the
+                                 first one that runs uses match.any when the sum
+                                 of its squared digit shares exceeds
+                                 2^-adapt_later; 1..10, default 5 (1/32) */
+    int adapt_first;          /* the same threshold for the first pass that
+                                 runs, which sees the input order; 1..10,
+                                 default 2 (1/4) */
+    int seg_warp_cap;         /* segmented sort: segments shorter than this are
+                                 sorted by one warp in registers; 32, 64, 128 or
+                                 256 (default 256) */
+    int small_cap;            /* lone arrays of at most this many keys are sorted
+                                 by one CTA in shared memory in a single launch
+                                 with no scratch memory (the GPU form of the
+                                 paper's small-array fallback, Algorithm 5);
+                                 0 = default: 4096 when algo is AUTO, else off;
+                                 1 = off; 2..8192 = that cut-over, whatever the
+                                 algo */
+    long long seg_giant;      /* segmented sort: segments longer than this many
+                                 keys are sorted one by one by the device-wide
+                                 radix path; finding them costs one small
+                                 synchronous read of the length histogram, so it
+                                 is skipped while the stream is being captured
+                                 into a CUDA graph; 0 = default (2^24), -1 =
+                                 never */
 } evosort_params;
 
 /* Fills *p with the built-in defaults (radix, d = 8, no workspace, NULL stream). */
@@ -207,7 +230,12 @@ typedef enum {
     EVOSORT_CLASS_SORTED = 4,    /* >= 90% of the unequal sampled neighbours rise */
     EVOSORT_CLASS_REVERSE = 5,   /* >= 90% of the unequal sampled neighbours fall */
     EVOSORT_CLASS_CONSTANT = 6,  /* one value */
-    EVOSORT_CLASS_NARROW16 = 7   /* at most 16 key bits vary */
+    EVOSORT_CLASS_NARROW16 = 7,  /* at most 16 key bits vary */
+    EVOSORT_CLASS_SEGMENTED = 8  /* table entries for batched segmented sorts,
+                                    keyed by the batch's total key count; used
+                                    by evosort_segmented_sort when params is
+                                    NULL or params->algo is AUTO (no sample is
+                                    read) */
 } evosort_dist_class;
 
 /* Class of keys[0..n) from a strided sample (synchronises the stream). */
@@ -253,6 +281,17 @@ typedef struct {
     int tins_init_max;       /* 256: first-generation insertion threshold bound */
     int allow_merge;         /* 1: the algorithm gene may pick mergesort */
     uint64_t seed;           /* 42 */
+    int mode;                /* 0: genomes for the sort of one array (algorithm,
+                                digit width, pass kernel, tile shape, ranking,
+                                adaptive-ranking thresholds, insertion threshold,
+                                small-array cut-over); 1: genomes for a batched
+                                segmented sort (warp-tier, block-tier and giant
+                                cut-overs, insertion threshold).  evosort_tune
+                                sets 0. */
+    uint64_t sample_keys;    /* keys of the array being tuned (mode 0; 0 =
+                                unknown): genomes whose small-array cut-over is
+                                at or above it all take the one-CTA path and
+                                share one evaluation */
 } evosort_ga_config;
 
 typedef struct {
@@ -283,14 +322,17 @@ evosort_status evosort_tune(const void* sample, size_t n, evosort_dtype dt, cons
  * running inside another framework's execute callback (a server plugin or a
  * custom operator) whose host framework owns all device memory and forbids
  * allocation calls, or latency-critical loops that must not block in the
- * allocator.  Same result as evosort_sort_to with default parameters
- * (LSD radix sort, Algorithms 4a/4b).  keys_in/keys_out: DEVICE arrays of n
- * keys of dtype dt; they may be equal (in place) but must not otherwise
- * overlap.  stream: cudaStream_t (NULL = legacy default stream).
- * Scratch: a fixed 64 MiB buffer inside the library's device image, held by
- * every device that loads the library until the process exits.  Sizes whose
- * scratch exceeds it (about 7.4 million 64-bit or 15.7 million 32-bit keys) are
- * rejected with EVOSORT_ERR_INVALID before anything is launched.
+ * allocator.  The result is the one evosort_sort_to gives with default
+ * parameters, and the kernels and tile shape are the ones it picks for n
+ * keys.  keys_in/keys_out: DEVICE arrays of n keys of dtype dt; they may be
+ * equal (in place) but must not otherwise overlap.  stream: cudaStream_t
+ * (NULL = legacy default stream).
+ * Scratch: a fixed 64 MiB buffer inside the library's device image, reserved
+ * on each device the first time this entry point runs there (or when the
+ * library's module is loaded, if the CUDA runtime's lazy loading is off) and
+ * held until the process exits.  Sizes whose scratch exceeds it (above about
+ * 7.7 million 64-bit or 15.8 million 32-bit keys) are rejected with
+ * EVOSORT_ERR_INVALID before anything is launched.
  * The first call on each device looks up the buffer's device address (once,
  * with that device current); make that first call before any stream capture.
  * Every call on a device shares the one buffer: calls whose work overlaps on
@@ -306,6 +348,14 @@ evosort_status evosort_sort_noalloc(const void* keys_in, void* keys_out, size_t 
  * radix scatter offset fell outside the array, whose stores the kernel skips;
  * EVOSORT_ERR_INVALID for bad segment offsets), then clears it. */
 evosort_status evosort_sync(void* stream);
+
+/* Poll limit of the bounded device-side waits on look-back slots, for tests
+ * of the failure path and for debugging (the paper has no counterpart).
+ * polls == 0 restores the built-in limit (2^22 polls, about a second).  A
+ * wait that runs out records EVOSORT_ERR_TIMEOUT for the next evosort_sync
+ * and its kernel returns; that sort's output is then invalid.  Applies to
+ * sorts enqueued after the call, process-wide. */
+void evosort_set_wait_limit(uint32_t polls);
 
 /* Message describing the calling thread's last error ("" if none). */
 const char* evosort_last_error(void);
@@ -327,7 +377,8 @@ typedef enum {
     EVOSORT_K_MERGE_BLOCK = 4,       /* insertion-sorted runs merged in a tile */
     EVOSORT_K_MERGE_PARTITION = 5,   /* merge-path split points */
     EVOSORT_K_MERGE_PASS = 6,        /* one pairwise merge round */
-    EVOSORT_K_SEGMENTED = 7          /* batched segmented sort kernels */
+    EVOSORT_K_SEGMENTED = 7,         /* batched segmented sort kernels */
+    EVOSORT_K_SMALL = 8              /* one-CTA shared-memory sort of a small array */
 } evosort_kernel_kind;
 
 typedef struct {

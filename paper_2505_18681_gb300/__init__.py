@@ -21,7 +21,7 @@ import torch
 
 from . import _build
 
-__all__ = ["sort", "sort_pairs", "segmented_sort", "sync", "workspace_bytes", "kernel_launches",
+__all__ = ["sort", "sort_pairs", "segmented_sort", "sync", "workspace_bytes", "kernel_launches", "set_wait_limit",
            "profile", "profile_read",
            "EvoSortError", "Params", "library", "DTYPES"]
 
@@ -44,7 +44,9 @@ class Params(ctypes.Structure):
                 ("block_size", ctypes.c_int), ("insertion_threshold", ctypes.c_int),
                 ("rank_mode", ctypes.c_int), ("seg_block_cap", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t), ("descending", ctypes.c_int), ("pass_kernel", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_size_t), ("descending", ctypes.c_int), ("pass_kernel", ctypes.c_int),
+                ("adapt_later", ctypes.c_int), ("adapt_first", ctypes.c_int), ("seg_warp_cap", ctypes.c_int),
+                ("small_cap", ctypes.c_int), ("seg_giant", ctypes.c_longlong)]
 
 
 class GAConfig(ctypes.Structure):
@@ -52,7 +54,8 @@ class GAConfig(ctypes.Structure):
     _fields_ = [("population", ctypes.c_int), ("generations", ctypes.c_int), ("crossover_p", ctypes.c_double),
                 ("mutation_p", ctypes.c_double), ("gene_mutation_p", ctypes.c_double), ("elite", ctypes.c_int),
                 ("tournament", ctypes.c_int), ("reps", ctypes.c_int), ("tins_init_max", ctypes.c_int),
-                ("allow_merge", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("allow_merge", ctypes.c_int), ("seed", ctypes.c_uint64), ("mode", ctypes.c_int),
+                ("sample_keys", ctypes.c_uint64)]
 
 
 class GALog(ctypes.Structure):
@@ -64,10 +67,11 @@ class GALog(ctypes.Structure):
 FitnessFn = ctypes.CFUNCTYPE(ctypes.c_float, ctypes.POINTER(Params), ctypes.c_float, ctypes.c_void_p)
 
 CLASSES = {0: "random", 1: "skewed", 2: "narrow", 3: "few", 4: "sorted", 5: "reverse", 6: "constant",
-           7: "narrow16"}
+           7: "narrow16", 8: "segmented"}
 CLASS_CODE = {v: k for k, v in CLASSES.items()}
 PARAM_FIELDS = ("algo", "digit_bits", "keys_per_thread", "block_size", "insertion_threshold", "rank_mode",
-                "seg_block_cap")
+                "seg_block_cap", "pass_kernel", "adapt_later", "adapt_first", "seg_warp_cap", "small_cap",
+                "seg_giant")
 
 
 class KernelRecord(ctypes.Structure):
@@ -78,7 +82,7 @@ class KernelRecord(ctypes.Structure):
 
 
 KERNEL_KINDS = {0: "radix_histogram", 1: "radix_scan", 2: "radix_onesweep", 3: "radix_fixup",
-                4: "merge_block", 5: "merge_partition", 6: "merge_pass", 7: "segmented"}
+                4: "merge_block", 5: "merge_partition", 6: "merge_pass", 7: "segmented", 8: "small"}
 
 _lock = threading.Lock()
 _lib = None
@@ -144,6 +148,8 @@ def library():
             lib.evosort_profile_read.restype = sz
             lib.evosort_kernel_launches.argtypes = []
             lib.evosort_kernel_launches.restype = ctypes.c_uint64
+            lib.evosort_set_wait_limit.argtypes = [ctypes.c_uint32]
+            lib.evosort_set_wait_limit.restype = None
             _lib = lib
     return _lib
 
@@ -183,7 +189,8 @@ def _stream_handle(stream) -> int:
 
 def make_params(algo=None, digit_bits=0, keys_per_thread=0, block_size=0, insertion_threshold=0,
                 rank_mode=0, seg_block_cap=0, stream=None, workspace: torch.Tensor | None = None,
-                descending=False, pass_kernel=0) -> Params:
+                descending=False, pass_kernel=0, adapt_later=0, adapt_first=0, seg_warp_cap=0, small_cap=0,
+                seg_giant=0) -> Params:
     p = Params()
     library().evosort_default_params(ctypes.byref(p))
     p.algo = ALGOS[algo]
@@ -195,6 +202,11 @@ def make_params(algo=None, digit_bits=0, keys_per_thread=0, block_size=0, insert
     p.seg_block_cap = int(seg_block_cap or 0)
     p.descending = 1 if descending else 0
     p.pass_kernel = int(pass_kernel or 0)
+    p.adapt_later = int(adapt_later or 0)
+    p.adapt_first = int(adapt_first or 0)
+    p.seg_warp_cap = int(seg_warp_cap or 0)
+    p.small_cap = int(small_cap or 0)
+    p.seg_giant = int(seg_giant or 0)
     p.stream = _stream_handle(stream)
     if workspace is not None:
         p.workspace = workspace.data_ptr()
@@ -288,6 +300,12 @@ def sync(stream=None) -> None:
 def workspace_bytes(n: int, dtype: torch.dtype, with_values: bool = False, **kw) -> int:
     p = make_params(**kw)
     return int(library().evosort_workspace_bytes(n, DTYPES[dtype], int(with_values), ctypes.byref(p)))
+
+
+def set_wait_limit(polls: int) -> None:
+    """Poll limit of the device-side look-back waits (0 = built-in default);
+    for tests of the failure path."""
+    library().evosort_set_wait_limit(int(polls))
 
 
 def kernel_launches() -> int:

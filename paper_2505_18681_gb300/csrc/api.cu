@@ -1,6 +1,7 @@
 // C ABI of the sort library: argument checks, parameter resolution, scratch
 // memory and the dispatcher of Algorithm 5 (AdaptivePartitionSort).
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -19,6 +20,12 @@ __device__ uint32_t g_status_word;
 
 static thread_local std::string t_err;
 static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint32_t> g_wait_limit{0};
+
+uint32_t wait_limit() {
+    const uint32_t v = g_wait_limit.load(std::memory_order_relaxed);
+    return v ? v : kSpinLimit;
+}
 
 void set_error(const std::string& msg) { t_err = msg; }
 void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -211,6 +218,9 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     const bool adapt = pl.rank_mode == 4 && n >= kAdaptMinKeys;
     const int rank = pl.rank_mode == 4 ? 3 : pl.rank_mode;
     a.adapt = adapt ? 1 : 0;
+    a.conc_later = std::ldexp(1.0, -pl.adapt_later);
+    a.conc_first = std::ldexp(1.0, -pl.adapt_first);
+    a.spin_limit = wait_limit();
     a.ntiles = L.ntiles;
     a.desc = (PassDesc*)(base + L.off_desc);
     a.counts = (unsigned long long*)(base + L.off_counts);
@@ -283,6 +293,11 @@ static void defaults_for(int w, Plan* pl) {
     pl->seg_block_cap = w == 4 ? 8192 : 4096;
     pl->descending = false;
     pl->pass_kernel = 0;   // chosen with the tile shape
+    pl->adapt_later = 5;   // 1/32
+    pl->adapt_first = 2;   // 1/4
+    pl->seg_warp_cap = 256;
+    pl->small_cap = kSmallDefault;
+    pl->seg_giant = (long long)1 << 24;
 }
 
 // Register-tile shapes in order of preference per key width and form, and
@@ -386,6 +401,27 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
         *err = "params.pass_kernel must be 0, 1 or 2";
         return EVOSORT_ERR_INVALID;
     }
+    if (p->adapt_later) pl->adapt_later = p->adapt_later;
+    if (p->adapt_first) pl->adapt_first = p->adapt_first;
+    if (pl->adapt_later < 1 || pl->adapt_later > 10 || pl->adapt_first < 1 || pl->adapt_first > 10) {
+        *err = "params.adapt_later / adapt_first must be in [1, 10]";
+        return EVOSORT_ERR_INVALID;
+    }
+    if (p->seg_warp_cap) pl->seg_warp_cap = p->seg_warp_cap;
+    if (pl->seg_warp_cap != 32 && pl->seg_warp_cap != 64 && pl->seg_warp_cap != 128 && pl->seg_warp_cap != 256) {
+        *err = "params.seg_warp_cap must be 32, 64, 128 or 256";
+        return EVOSORT_ERR_INVALID;
+    }
+    if (p->small_cap) pl->small_cap = p->small_cap;
+    if (pl->small_cap < 1 || pl->small_cap > kSmallMax) {
+        *err = "params.small_cap must be 0 (default), 1 (off) or at most 8192";
+        return EVOSORT_ERR_INVALID;
+    }
+    if (p->seg_giant) pl->seg_giant = p->seg_giant;
+    if (pl->seg_giant != -1 && (pl->seg_giant < 1024 || (pl->seg_giant & (pl->seg_giant - 1)))) {
+        *err = "params.seg_giant must be 0 (default), -1 (off) or a power of two of at least 1024";
+        return EVOSORT_ERR_INVALID;
+    }
     if (p->rank_mode) pl->rank_mode = p->rank_mode;
     else if (pl->digit_bits > 8) pl->rank_mode = 2;   // match masks are compiled for d <= 8
     else if (pl->digit_bits < 8) pl->rank_mode = 3;   // match.any is compiled for d = 8
@@ -423,10 +459,12 @@ static int resolve(const evosort_params* p, int dt, bool pairs, Plan* pl, std::s
 static bool valid_dtype(int dt) { return dt >= EVOSORT_I32 && dt <= EVOSORT_F64; }
 
 namespace evosort {
-// The built-in parameters of a keys-only radix sort of dtype dt.
-void default_radix_plan(int dt, Plan* pl) {
+// The built-in parameters of a keys-only radix sort of n keys of dtype dt
+// (n = 0: the tile shape for large inputs).
+void default_radix_plan(int dt, Plan* pl, size_t n) {
     std::string err;
-    resolve(nullptr, dt, false, pl, &err);
+    resolve(nullptr, dt, false, pl, &err, n);
+    pl->algo = EVOSORT_ALGO_RADIX;
 }
 }  // namespace evosort
 
@@ -459,7 +497,27 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     if (pairs && (in == out) != ((const void*)vin == (const void*)vout))
         return finish(EVOSORT_ERR_INVALID, "keys and values must both be in place or both out of place");
     if (n >= (1ull << 40)) return finish(EVOSORT_ERR_UNSUPPORTED, "n >= 2^40");
+    if (n == 1) {   // one key is sorted: in place nothing to do, else one copy
+        cudaStream_t s1 = p ? (cudaStream_t)p->stream : nullptr;
+        cudaError_t e1 = cudaSuccess;
+        if (in != out) e1 = cudaMemcpyAsync(out, in, w, cudaMemcpyDeviceToDevice, s1);
+        if (e1 == cudaSuccess && pairs && vin != vout) e1 = cudaMemcpyAsync(vout, vin, 4, cudaMemcpyDeviceToDevice, s1);
+        if (e1 != cudaSuccess) return finish(EVOSORT_ERR_CUDA, std::string("copy: ") + cudaGetErrorString(e1));
+        return EVOSORT_OK;
+    }
     if (pairs && n > 0xFFFFFFFFull) return finish(EVOSORT_ERR_UNSUPPORTED, "key/value sorts need n < 2^32");
+    // Algorithm 5's small-array branch: when the caller leaves the choice to
+    // the dispatcher, arrays of at most small_cap keys are sorted by one CTA
+    // in shared memory (one launch, no scratch, no sample of the keys)
+    if (!p || p->algo == EVOSORT_ALGO_AUTO || p->small_cap > 1) {
+        Plan sp;
+        int rc0 = resolve(p, dt, pairs, &sp, &err, n);
+        if (rc0) return finish(rc0, err);
+        if (sp.small_cap > 1 && n <= (size_t)sp.small_cap) {
+            rc0 = small_sort(in, out, vin, vout, n, dt, sp, p ? (cudaStream_t)p->stream : nullptr, &err);
+            return finish(rc0, err);
+        }
+    }
     // dispatcher: tuned parameters for this input when the caller leaves the choice open
     evosort_params planned;
     if ((!p || p->algo == EVOSORT_ALGO_AUTO) && table_nonempty()) {
@@ -577,6 +635,26 @@ evosort_status evosort_segmented_sort(void* keys, size_t total, const uint64_t* 
     if ((uintptr_t)keys % w) return finish(EVOSORT_ERR_INVALID, "misaligned key pointer");
     if (nseg >= 0xFFFFFFFFull) return finish(EVOSORT_ERR_UNSUPPORTED, "nseg >= 2^32");
     if (total >= (1ull << 40)) return finish(EVOSORT_ERR_UNSUPPORTED, "total >= 2^40");
+    // tuned tier cut-overs for batches of this size when the caller leaves
+    // the choice open
+    evosort_params planned;
+    if ((!p || p->algo == EVOSORT_ALGO_AUTO) && table_nonempty()) {
+        evosort_default_params(&planned);
+        planned.algo = EVOSORT_ALGO_AUTO;
+        if (table_lookup(dt, total, EVOSORT_CLASS_SEGMENTED, &planned)) {
+            if (p) {
+                planned.stream = p->stream;
+                planned.workspace = p->workspace;
+                planned.workspace_bytes = p->workspace_bytes;
+                planned.descending = p->descending;
+            } else {
+                planned.stream = nullptr;
+                planned.workspace = nullptr;
+                planned.workspace_bytes = 0;
+            }
+            p = &planned;
+        }
+    }
     Plan pl;
     int rc = resolve(p, dt, false, &pl, &err);
     if (rc) return finish(rc, err);
@@ -598,7 +676,7 @@ evosort_status evosort_segmented_sort(void* keys, size_t total, const uint64_t* 
     } else if ((uintptr_t)ws % 256) {
         return finish(EVOSORT_ERR_INVALID, "workspace must be 256-byte aligned");
     }
-    rc = segmented_sort(keys, total, offsets, nseg, dt, pl, ws, ws_bytes, s, &err);
+    rc = segmented_sort(keys, total, offsets, nseg, dt, pl, ws, ws_bytes, !owned, s, &err);
     if (owned) cudaFreeAsync(ws, s);
     return finish(rc, err);
 }
@@ -626,6 +704,8 @@ evosort_status evosort_sync(void* stream) {
 }
 
 const char* evosort_last_error(void) { return t_err.c_str(); }
+
+void evosort_set_wait_limit(uint32_t polls) { g_wait_limit.store(polls, std::memory_order_relaxed); }
 
 evosort_status evosort_profile(int enable) {
     std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -21,11 +21,27 @@ struct Plan {
     int rank_mode;            // radix tile ranking variant
     int seg_block_cap;        // segmented sort: longest segment sorted in shared memory
     bool descending;          // non-increasing order
-    int pass_kernel;          // radix pass kernel: 1 staged tile, 2/3 register tile (1/2 chains per warp)
+    int pass_kernel;          // radix pass kernel: 0 not chosen yet, 1 staged tile, 2 register tile
+    int adapt_later;          // adaptive ranking thresholds, as -log2 of the concentration
+    int adapt_first;
+    int seg_warp_cap;         // segmented sort: warp tier below this length
+    int small_cap;            // single-CTA path for lone arrays up to this size (1 = off)
+    long long seg_giant;      // segmented sort: device-wide path above this length (-1 = off)
 };
 
+// Single-CTA path for lone small arrays (Algorithm 5's small-array branch):
+// default and largest cut-over, in keys.
+constexpr int kSmallDefault = 4096;
+constexpr int kSmallMax = 8192;
+int small_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt, const Plan& pl,
+               cudaStream_t s, std::string* err);
+
+// Poll limit of the bounded device-side waits (look-back slots); set by
+// evosort_set_wait_limit, 0 = the built-in default.
+uint32_t wait_limit();
+
 void set_error(const std::string& msg);
-void default_radix_plan(int dt, Plan* pl);
+void default_radix_plan(int dt, Plan* pl, size_t n = 0);
 bool table_nonempty();
 int classify_sample(const unsigned char* buf, size_t m, int dt, bool descending = false);
 int classify_host(const void* keys, size_t n, int dt, bool descending = false);
@@ -62,7 +78,7 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
 
 size_t segmented_workspace_bytes(size_t total, size_t nseg, int w);
 int segmented_sort(void* keys, size_t total, const uint64_t* off, size_t nseg, int dt, const Plan& pl, void* ws,
-                   size_t ws_bytes, cudaStream_t s, std::string* err);
+                   size_t ws_bytes, bool caller_ws, cudaStream_t s, std::string* err);
 
 size_t merge_workspace_bytes(size_t n, int w, bool pairs, const Plan& pl);
 int merge_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt,

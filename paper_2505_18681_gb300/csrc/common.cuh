@@ -14,8 +14,10 @@ enum : int { DT_I32 = 0, DT_I64 = 1, DT_U32 = 2, DT_U64 = 3, DT_F32 = 4, DT_F64 
 // device status word bits (evosort_sync maps them to evosort_status)
 enum : uint32_t { ST_TIMEOUT = 1u, ST_BAD_OFFSETS = 2u, ST_RANGE = 4u };
 
-// Bounded waits: polls of a look-back slot before the kernel gives up, records
-// ST_TIMEOUT and proceeds (its output is then invalid but the context lives).
+// Bounded waits: polls before a kernel gives up, records ST_TIMEOUT and
+// proceeds (its output is then invalid but the context lives).  Look-back
+// waits take their limit from the launch (evosort_set_wait_limit, default
+// this value); mbarrier waits for the kernel's own bulk copies always use it.
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 inline int dtype_bytes(int dt) { return (dt == DT_I32 || dt == DT_U32 || dt == DT_F32) ? 4 : 8; }

@@ -106,7 +106,7 @@ bool table_lookup(int dt, size_t n, int cls, evosort_params* out) {
     std::lock_guard<std::mutex> lk(g_tab_mu);
     const Entry* best = nullptr;
     int bestd = 1 << 30;
-    for (int pass = 0; pass < 2 && !best; ++pass) {
+    for (int pass = 0; pass < (cls == EVOSORT_CLASS_SEGMENTED ? 1 : 2) && !best; ++pass) {
         const int want = pass == 0 ? cls : EVOSORT_CLASS_RANDOM;
         for (const auto& x : g_tab)
             if (x.dt == dt && x.cls == want && std::abs(x.bucket - bucket) < bestd) {
@@ -186,7 +186,7 @@ evosort_status evosort_classify(const void* keys, size_t n, evosort_dtype dt, vo
 
 evosort_status evosort_table_set(evosort_dtype dt, int size_bucket, int cls, const evosort_params* p, float ms) {
     if (!p || dt < EVOSORT_I32 || dt > EVOSORT_F64 || size_bucket < 0 || size_bucket > 63 || cls < 0 ||
-        cls > EVOSORT_CLASS_NARROW16) {
+        cls > EVOSORT_CLASS_SEGMENTED) {
         set_error("evosort_table_set: bad argument");
         return EVOSORT_ERR_INVALID;
     }
@@ -222,11 +222,14 @@ evosort_status evosort_table_save(const char* path) {
         return EVOSORT_ERR_INVALID;
     }
     f << "# evosort tuned table: dtype size_bucket class algo digit_bits block_size keys_per_thread "
-         "rank_mode insertion_threshold seg_block_cap ms\n";
+         "rank_mode insertion_threshold seg_block_cap ms [pass_kernel adapt_later adapt_first seg_warp_cap "
+         "small_cap seg_giant]\n";
     for (const auto& x : g_tab)
         f << x.dt << ' ' << x.bucket << ' ' << x.cls << ' ' << x.p.algo << ' ' << x.p.digit_bits << ' '
           << x.p.block_size << ' ' << x.p.keys_per_thread << ' ' << x.p.rank_mode << ' '
-          << x.p.insertion_threshold << ' ' << x.p.seg_block_cap << ' ' << x.ms << '\n';
+          << x.p.insertion_threshold << ' ' << x.p.seg_block_cap << ' ' << x.ms << ' ' << x.p.pass_kernel << ' '
+          << x.p.adapt_later << ' ' << x.p.adapt_first << ' ' << x.p.seg_warp_cap << ' ' << x.p.small_cap << ' '
+          << x.p.seg_giant << '\n';
     return f ? EVOSORT_OK : EVOSORT_ERR_INVALID;
 }
 
@@ -251,6 +254,22 @@ evosort_status evosort_table_load(const char* path) {
             set_error("evosort_table_load: malformed line " + std::to_string(lineno));
             return EVOSORT_ERR_INVALID;
         }
+        // optional later columns (0 = default when absent)
+        int extra[5] = {0, 0, 0, 0, 0};
+        long long giant = 0;
+        int got = 0;
+        while (got < 5 && (is >> extra[got])) ++got;
+        if (got == 5) is >> giant;
+        if (!is.eof() && is.fail() && got > 0 && got < 5) {
+            set_error("evosort_table_load: malformed optional columns on line " + std::to_string(lineno));
+            return EVOSORT_ERR_INVALID;
+        }
+        p.pass_kernel = extra[0];
+        p.adapt_later = extra[1];
+        p.adapt_first = extra[2];
+        p.seg_warp_cap = extra[3];
+        p.small_cap = extra[4];
+        p.seg_giant = giant;
         const evosort_status st = evosort_table_set((evosort_dtype)dt, bucket, cls, &p, ms);
         if (st != EVOSORT_OK) return st;
     }

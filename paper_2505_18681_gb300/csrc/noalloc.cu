@@ -6,7 +6,10 @@
 // memory and forbids allocation calls, or a latency-critical loop that must
 // not block in the allocator or fail with out-of-memory half way through.
 // This entry point serves them: its scratch space is a buffer of fixed size
-// in the library's own device image, set aside when the library is loaded.
+// in the library's own device image.  The CUDA runtime loads that image
+// lazily by default, so the buffer is reserved on each device the first time
+// this entry point runs there (or when the library's module is loaded, if
+// lazy loading is turned off), and it stays reserved until the process exits.
 #include <mutex>
 
 #include "evosort.h"
@@ -17,8 +20,8 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;   // 64 MiB per device
 
-// The scratch buffer.  Every device that loads the library holds one until the
-// process exits.  In host code this name only stands for the buffer; its
+// The scratch buffer.  Every device where it has been reserved holds one until
+// the process exits.  In host code this name only stands for the buffer; its
 // device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -52,7 +55,7 @@ extern "C" evosort_status evosort_sort_noalloc(const void* keys_in, void* keys_o
         return EVOSORT_ERR_INVALID;
     }
     Plan pl;
-    default_radix_plan(dt, &pl);
+    default_radix_plan(dt, &pl, n);   // the tile shape the allocating sort would pick for n keys
     const size_t need = radix_workspace_bytes(n, w, false, pl);
     if (need > kNoAllocScratchBytes) {
         set_error("evosort_sort_noalloc: " + std::to_string(n) + " keys need " + std::to_string(need) +

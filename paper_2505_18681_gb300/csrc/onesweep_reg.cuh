@@ -220,11 +220,11 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
             if (tile > 0) {
                 if (a.lb64) {
                     excl = lookback_digit<uint64_t, kRegLookback>((const uint64_t*)a.lookback + slot0, bins, tile,
-                                                                  a.status);
+                                                                  a.status, a.spin_limit);
                     st_relaxed((uint64_t*)a.lookback + slot, FP64 | (excl + cnt));
                 } else {
                     excl = lookback_digit<uint32_t, kRegLookback>((const uint32_t*)a.lookback + slot0, bins, tile,
-                                                                  a.status);
+                                                                  a.status, a.spin_limit);
                     st_relaxed((uint32_t*)a.lookback + slot, FP32 | (uint32_t)(excl + cnt));
                 }
             }

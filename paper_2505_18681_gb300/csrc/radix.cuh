@@ -52,6 +52,8 @@ struct RadixArgs {
     int npass;       // ceil(8w / d)
     int lb64;        // look-back slots are 64-bit (n >= 2^30)
     int adapt;       // ranking chosen per pass by K2 (PassDesc::rank)
+    double conc_later, conc_first;   // adaptive ranking thresholds (see radix_scan_plan)
+    uint32_t spin_limit;             // polls of a look-back slot before a wait gives up
     size_t ntiles;   // tiles per pass
     PassDesc* desc;             // npass + 1 entries
     unsigned long long* counts; // npass << d digit counts, then exclusive offsets
@@ -196,10 +198,9 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
 // over digits of (count / n)^2: when it is high, most lanes of a warp share a
 // few digits, which serialises the match masks' shared atomics.  A later pass
 // sees keys already grouped by the lower digits, so equal digits sit together
-// and 1/32 is the threshold; the first pass to run sees the input order, where
-// match.any only pays once one digit holds most keys (threshold 1/4).
-constexpr double kConcentrated = 1.0 / 32.0;
-constexpr double kConcentratedFirst = 1.0 / 4.0;
+// and the threshold is low (default 1/32, a.conc_later); the first pass to run
+// sees the input order, where match.any only pays once one digit holds most
+// keys (default 1/4, a.conc_first).  Both thresholds are tunable.
 
 static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int inplace) {
     __shared__ unsigned long long s_scr[33];
@@ -228,7 +229,7 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
             double t = 0.0;
             for (int w = 0; w < 32; ++w) t += s_sq[w];
             const double nn = (double)a.n * (double)a.n;
-            s_conc[p] = (t > kConcentrated * nn ? 1 : 0) | (t > kConcentratedFirst * nn ? 2 : 0);
+            s_conc[p] = (t > a.conc_later * nn ? 1 : 0) | (t > a.conc_first * nn ? 2 : 0);
         }
         unsigned long long tot;
         unsigned long long ex = block_exclusive_scan<1024>(sum, s_scr, &tot);
@@ -335,7 +336,7 @@ __host__ __device__ constexpr size_t onesweep_smem_bytes(int block, int kpt, int
 // back to the nearest inclusive prefix.  LBW slots are read per L2 round trip.
 template <typename S, int LBW>
 __device__ __forceinline__ uint64_t lookback_digit(const S* slot0, size_t stride, long long tile,
-                                                   uint32_t* status) {
+                                                   uint32_t* status, uint32_t limit) {
     constexpr int FB = sizeof(S) * 8 - 2;   // flag bits: 01 aggregate, 10 inclusive prefix
     const S cmask = ((S)1 << FB) - 1;
     uint64_t excl = 0;
@@ -364,7 +365,7 @@ __device__ __forceinline__ uint64_t lookback_digit(const S* slot0, size_t stride
         if (fin) break;
         t -= adv;
         if (blocked) {
-            if (++polls > kSpinLimit) {
+            if (++polls > limit) {
                 atomicOr(status, ST_TIMEOUT);
                 break;
             }
@@ -709,12 +710,12 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     if (tile > 0) {
                         if (a.lb64) {
                             excl = lookback_digit<uint64_t, 16>((const uint64_t*)a.lookback + slot0, bins,
-                                                               tile, a.status);
+                                                               tile, a.status, a.spin_limit);
                             st_relaxed((uint64_t*)a.lookback + slot0 + (size_t)tile * bins,
                                        FP64 | (excl + s_tcnt[b]));
                         } else {
                             excl = lookback_digit<uint32_t, 16>((const uint32_t*)a.lookback + slot0, bins,
-                                                               tile, a.status);
+                                                               tile, a.status, a.spin_limit);
                             st_relaxed((uint32_t*)a.lookback + slot0 + (size_t)tile * bins,
                                        FP32 | (uint32_t)(excl + s_tcnt[b]));
                         }

@@ -1,8 +1,9 @@
 // Batched segmented sort: many independent arrays of uneven length sorted in
 // one persistent launch.  Each segment is sorted with the method its length
 // calls for:
-//   warp tier   (len < 256)          one warp, keys in registers, bitonic
-//                                    network across the warp's lanes;
+//   warp tier   (len < warp cap)     one warp, keys in registers, bitonic
+//                                    network across the warp's lanes (warp cap
+//                                    32..256, a tuning parameter);
 //   block tier  (len <= block cap)   one CTA, keys in shared memory, the
 //                                    insertion-run + merge sort of Algorithm 3;
 //   large tier  (len >  block cap)   one CTA runs the LSD radix sort of
@@ -11,9 +12,19 @@
 //                                    then per 8-bit digit a stable tile-by-tile
 //                                    scatter.  A single CTA walks the tiles in
 //                                    order, so running digit offsets replace the
-//                                    device-wide look-back.
+//                                    device-wide look-back;
+//   giant tier  (len >= giant)       the device-wide radix sort, one segment at
+//                                    a time, before the persistent launch (one
+//                                    CTA per segment would leave the rest of the
+//                                    GPU idle once the other segments are done).
 // K7 seg_count / seg_scan / seg_fill put the segments in a work list, longest
-// first (counting sort by floor(log2(len))); K8 seg_sort drains it.
+// first (counting sort by floor(log2(len))); K8 seg_sort drains it.  Giant
+// segments are the head of that list: the host reads the list's length
+// histogram (one small synchronous copy), sorts the head segments with the
+// device-wide path and has K8 start after them.
+#include <algorithm>
+#include <vector>
+
 #include "evosort.h"
 #include "api_internal.h"
 #include "common.cuh"
@@ -24,8 +35,7 @@ namespace {
 
 constexpr int kSB = 512;             // threads per CTA
 constexpr int kSW = kSB / 32;        // warps per CTA
-constexpr int kWKW = 8;              // keys per lane in the warp tier
-constexpr int kWarpCap = 32 * kWKW;  // warp tier: len < kWarpCap
+constexpr int kWKW = 8;              // keys per lane in the warp tier (at most 256 keys)
 constexpr int kNB = 48;              // length buckets (floor log2)
 constexpr int kLKPT = 8;             // keys per thread per large-tier tile
 constexpr int kLTile = kSB * kLKPT;  // keys per large-tier tile
@@ -43,6 +53,8 @@ struct SegArgs {
     uint32_t* status;
     int block_cap;      // keys one CTA sorts in shared memory
     int tins;           // base run of the shared-memory merge sort
+    int warp_log2;      // warp tier: len < 2^warp_log2
+    uint32_t skip;      // work items sorted before K8 (giant segments)
 };
 
 __device__ __forceinline__ int len_bucket(uint64_t len) { return 63 - __clzll((long long)len); }
@@ -76,7 +88,7 @@ __global__ void seg_scan(SegArgs a) {
     for (int b = kNB - 1; b >= 1; --b) {
         a.hdr[kNB + b] = pos;
         pos += a.hdr[b];
-        if ((1ull << b) >= (uint64_t)kWarpCap)
+        if (b >= a.warp_log2)
             single += a.hdr[b];
         else
             warp += a.hdr[b];
@@ -276,6 +288,7 @@ __global__ void __launch_bounds__(kSB, 2) seg_sort(SegArgs a) {
         const uint32_t item = s_item;
         __syncthreads();
         if (item >= single + nbatch) break;
+        if (item < a.skip) continue;   // sorted by the device-wide path
         if (item < single) {
             const uint32_t seg = a.order[item];
             const uint64_t lo = a.off[seg], len = a.off[seg + 1] - lo;
@@ -294,6 +307,15 @@ __global__ void __launch_bounds__(kSB, 2) seg_sort(SegArgs a) {
     }
 }
 
+// (lo, len) of the first `count` work items (the longest segments).
+__global__ void seg_head(SegArgs a, uint32_t count, unsigned long long* out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint32_t seg = a.order[i];
+    out[2 * i] = a.off[seg];
+    out[2 * i + 1] = a.off[seg + 1] - a.off[seg];
+}
+
 size_t seg_smem_bytes(int w, int block_cap) {
     const size_t large = (size_t)w * 256 * 4 + 3 * 256 * 4 + kSW * 256 * 4 + kSW * 256 * 2 + (size_t)kLTile * w;
     const size_t block = (size_t)2 * block_cap * w;
@@ -308,8 +330,11 @@ size_t segmented_workspace_bytes(size_t total, size_t nseg, int w) {
     return seg_hdr_bytes() + (nseg * 4 + 255) / 256 * 256 + (total * w + 255) / 256 * 256;
 }
 
+static int segmented_giant(SegArgs& a, int dt, const Plan& pl, int gb, cudaStream_t s, uint32_t* skip,
+                           std::string* err);
+
 int segmented_sort(void* keys, size_t total, const uint64_t* off, size_t nseg, int dt, const Plan& pl, void* ws,
-                   size_t ws_bytes, cudaStream_t s, std::string* err) {
+                   size_t ws_bytes, bool caller_ws, cudaStream_t s, std::string* err) {
     const int w = dtype_bytes(dt);
     if (ws_bytes < segmented_workspace_bytes(total, nseg, w)) {
         *err = "workspace too small";
@@ -329,6 +354,8 @@ int segmented_sort(void* keys, size_t total, const uint64_t* off, size_t nseg, i
     a.status = status;
     a.block_cap = pl.seg_block_cap;
     a.tins = pl.insertion_threshold > 64 ? 16 : pl.insertion_threshold;
+    a.warp_log2 = 31 - __builtin_clz((unsigned)pl.seg_warp_cap);
+    a.skip = 0;
     const size_t smem = seg_smem_bytes(w, a.block_cap);
     const int sms = sm_count();
     cudaError_t e = cudaMemsetAsync(ws, 0, seg_hdr_bytes(), s);
@@ -342,6 +369,18 @@ int segmented_sort(void* keys, size_t total, const uint64_t* off, size_t nseg, i
             seg_fill<<<g, 256, 0, s>>>(a);
             e = cudaGetLastError();
         }
+    }
+    // giant tier: not while the stream is being captured (the length
+    // histogram read would synchronise), nor with a caller workspace (the
+    // device-wide path takes its own scratch)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (e == cudaSuccess && pl.seg_giant > 0 && !caller_ws && total >= (size_t)pl.seg_giant)
+        e = cudaStreamIsCapturing(s, &cap);
+    if (e == cudaSuccess && pl.seg_giant > 0 && !caller_ws && total >= (size_t)pl.seg_giant &&
+        cap == cudaStreamCaptureStatusNone) {
+        const int gb = 63 - __builtin_clzll((unsigned long long)pl.seg_giant);
+        const int rc = segmented_giant(a, dt, pl, gb, s, &a.skip, err);
+        if (rc != EVOSORT_OK) return rc;
     }
     {
         ProfScope ps(call, EVOSORT_K_SEGMENTED, 1, 2.0 * total * w, total, s);
@@ -373,6 +412,65 @@ int segmented_sort(void* keys, size_t total, const uint64_t* off, size_t nseg, i
         return EVOSORT_ERR_CUDA;
     }
     return EVOSORT_OK;
+}
+
+// Giant tier: after K7, count the segments of at least 2^gb keys from the
+// length histogram, sort each with the device-wide radix path (scratch from
+// the stream-ordered pool, sized for the longest), and return how many head
+// items K8 must skip.  Returns 0 items when there are none.
+static int segmented_giant(SegArgs& a, int dt, const Plan& pl, int gb, cudaStream_t s, uint32_t* skip,
+                           std::string* err) {
+    *skip = 0;
+    uint32_t hist[kNB];
+    cudaError_t e = cudaMemcpyAsync(hist, a.hdr, sizeof(hist), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        *err = std::string("segmented sort: length histogram read: ") + cudaGetErrorString(e);
+        return EVOSORT_ERR_CUDA;
+    }
+    uint32_t k = 0;
+    for (int b = gb; b < kNB; ++b) k += hist[b];
+    if (k == 0) return EVOSORT_OK;
+    std::vector<unsigned long long> head(2 * (size_t)k);
+    unsigned long long* d_head = nullptr;
+    e = cudaMallocAsync((void**)&d_head, head.size() * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        seg_head<<<(k + 255) / 256, 256, 0, s>>>(a, k, d_head);
+        count_launches(1);
+        e = cudaMemcpyAsync(head.data(), d_head, head.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(d_head, s);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *err = std::string("segmented sort: giant segment list: ") + cudaGetErrorString(e);
+        return EVOSORT_ERR_CUDA;
+    }
+    const int w = dtype_bytes(dt);
+    size_t longest = 0;
+    for (uint32_t i = 0; i < k; ++i) longest = std::max<size_t>(longest, head[2 * i + 1]);
+    Plan rp;
+    default_radix_plan(dt, &rp, longest);
+    rp.descending = pl.descending;
+    const size_t need = radix_workspace_bytes(longest, w, false, rp);
+    void* ws = nullptr;
+    e = cudaMallocAsync(&ws, need, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *err = std::string("segmented sort: giant segment scratch: ") + cudaGetErrorString(e);
+        return EVOSORT_ERR_NOMEM;
+    }
+    int rc = EVOSORT_OK;
+    for (uint32_t i = 0; i < k && rc == EVOSORT_OK; ++i) {
+        void* seg = (char*)a.keys + head[2 * i] * w;
+        Plan sp;
+        default_radix_plan(dt, &sp, head[2 * i + 1]);
+        sp.descending = pl.descending;
+        rc = radix_sort(seg, seg, nullptr, nullptr, head[2 * i + 1], dt, sp, ws, need, s, err);
+    }
+    cudaFreeAsync(ws, s);
+    *skip = k;
+    return rc;
 }
 
 }  // namespace evosort

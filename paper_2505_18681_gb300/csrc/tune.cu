@@ -51,20 +51,47 @@ struct Rng {
     int range(int lo, int hi) { return lo + (int)(next() % (uint64_t)(hi - lo + 1)); }
 };
 
+// Staged-tile shapes; register-tile shapes come from the library's
+// preference list for the key width (reg_shape_for).
 const int kShapes[][2] = {{256, 16}, {512, 16}, {512, 32}, {1024, 8}, {1024, 16}, {512, 8}};
 constexpr int kNShapes = 6;
+const int kSmallCaps[] = {1, 1024, 2048, 4096, 8192};   // 1 = off
+const int kBlockCaps[] = {256, 512, 1024, 2048, 4096, 8192};
+const int kWarpCaps[] = {32, 64, 128, 256};
+const long long kGiants[] = {-1, 1ll << 20, 1ll << 22, 1ll << 24, 1ll << 26};   // -1 = off
+
+// Tuning modes: one array (the sort of a sample), or a segmented batch.
+enum { MODE_ARRAY = 0, MODE_SEGMENTED = 1 };
 
 struct Genome {
-    int algo, d, shape, rank, tins;
-    bool operator<(const Genome& o) const {
-        return std::tie(algo, d, shape, rank, tins) < std::tie(o.algo, o.d, o.shape, o.rank, o.tins);
-    }
-    // genes that do not act on the chosen algorithm are normalised away so
-    // equivalent genomes share one fitness evaluation
-    Genome canon() const {
+    int algo, d, kern, shape, rank, tins, alater, afirst, small, sblock, swarp, sgiant;
+    auto key() const { return std::tie(algo, d, kern, shape, rank, tins, alater, afirst, small, sblock, swarp, sgiant); }
+    bool operator<(const Genome& o) const { return key() < o.key(); }
+    // genes that do not act in this mode, for this algorithm or at this size
+    // are normalised away, so equivalent genomes share one fitness evaluation
+    Genome canon(int mode, size_t n, int w) const {
         Genome g = *this;
-        if (algo == EVOSORT_ALGO_RADIX) g.tins = 0;
-        else g.d = g.shape = g.rank = 0;
+        if (mode == MODE_SEGMENTED) {
+            g.algo = g.d = g.kern = g.shape = g.rank = g.alater = g.afirst = g.small = 0;
+            if (g.tins > 64) g.tins = 16;   // the block tier's base runs
+            return g;
+        }
+        g.sblock = g.swarp = g.sgiant = 0;
+        if ((size_t)kSmallCaps[g.small] >= n && g.small != 0) {   // the one-CTA path takes the whole sort
+            g = Genome{};
+            g.algo = this->algo;   // kept: an explicit algorithm plus a cut-over selects the path
+            g.small = 4;           // every cap >= n behaves the same
+            g.tins = std::min(this->tins, 32);
+            return g;
+        }
+        g.small = 0;   // every cap < n is "off"
+        if (g.algo == EVOSORT_ALGO_RADIX) {
+            g.tins = 0;
+            if (g.kern == 2) g.shape %= (w == 4 ? 2 : 3);   // register shapes: a shorter list
+            if (g.rank != 4 || n < kAdaptMinKeys) g.alater = g.afirst = 0;
+        } else {
+            g.d = g.kern = g.shape = g.rank = g.alater = g.afirst = 0;
+        }
         return g;
     }
 };
@@ -73,20 +100,69 @@ Genome random_genome(Rng& r, int tins_hi) {
     Genome g;
     g.algo = r.unit() < 0.5 ? EVOSORT_ALGO_RADIX : EVOSORT_ALGO_MERGE;
     g.d = r.range(4, 11);
+    g.kern = r.range(1, 2);
     g.shape = r.range(0, kNShapes - 1);
     g.rank = r.range(1, 4);
     g.tins = r.range(2, tins_hi);
+    g.alater = r.range(3, 8);
+    g.afirst = r.range(1, 4);
+    g.small = r.range(0, 4);
+    g.sblock = r.range(0, 5);
+    g.swarp = r.range(0, 3);
+    g.sgiant = r.range(0, 4);
     return g;
 }
 
-void to_params(const Genome& g, evosort_params* p, void* stream) {
+// The library's defaults as a genome (seeded into the first generation).
+Genome default_genome(int w) {
+    Genome g;
+    g.algo = EVOSORT_ALGO_RADIX;
+    g.d = 8;
+    g.kern = 2;
+    g.shape = 0;
+    g.rank = 4;
+    g.tins = 32;
+    g.alater = 5;
+    g.afirst = 2;
+    g.small = 3;                  // 4096
+    g.sblock = w == 4 ? 5 : 4;    // 8192 / 4096
+    g.swarp = 3;                  // 256
+    g.sgiant = 3;                 // 2^24
+    return g;
+}
+
+// Register-tile shape `i` of the preference list for the key width.
+void reg_shape_for(int w, int i, int* block, int* kpt) {
+    static const int k4[][2] = {{1024, 16}, {512, 16}};
+    static const int k8[][2] = {{1024, 12}, {1024, 8}, {512, 8}};
+    if (w == 4) {
+        *block = k4[i % 2][0];
+        *kpt = k4[i % 2][1];
+    } else {
+        *block = k8[i % 3][0];
+        *kpt = k8[i % 3][1];
+    }
+}
+
+void to_params(const Genome& g, int w, evosort_params* p, void* stream) {
     evosort_default_params(p);
     p->algo = g.algo;
     p->digit_bits = g.d;
-    p->block_size = kShapes[g.shape][0];
-    p->keys_per_thread = kShapes[g.shape][1];
+    p->pass_kernel = g.kern;
+    if (g.kern == 2) {
+        reg_shape_for(w, g.shape, &p->block_size, &p->keys_per_thread);
+    } else if (g.kern == 1) {
+        p->block_size = kShapes[g.shape][0];
+        p->keys_per_thread = kShapes[g.shape][1];
+    }
     p->rank_mode = g.rank;
     p->insertion_threshold = g.tins;
+    p->adapt_later = g.alater;
+    p->adapt_first = g.afirst;
+    p->small_cap = g.small ? kSmallCaps[g.small] : 1;
+    p->seg_block_cap = g.sblock || g.swarp || g.sgiant ? kBlockCaps[g.sblock] : 0;
+    p->seg_warp_cap = g.sblock || g.swarp || g.sgiant ? kWarpCaps[g.swarp] : 0;
+    p->seg_giant = g.sblock || g.swarp || g.sgiant ? kGiants[g.sgiant] : 0;
     p->stream = stream;
 }
 
@@ -197,34 +273,38 @@ evosort_status evosort_ga_search(const evosort_ga_config* cfg, int key_bytes, ev
     else evosort_default_ga_config(&c);
     if (!fitness_cb || !best || (key_bytes != 4 && key_bytes != 8) || c.population < 4 || c.generations < 1 ||
         c.reps < 1 || c.tournament < 1 || c.elite < 0 || c.elite >= c.population || c.tins_init_max < 2 ||
-        c.tins_init_max > 2048) {
+        c.tins_init_max > 2048 || (c.mode != MODE_ARRAY && c.mode != MODE_SEGMENTED)) {
         set_error("evosort_ga_search: bad GA configuration");
         return EVOSORT_ERR_INVALID;
     }
     const int w = key_bytes;
+    const size_t n = c.sample_keys ? (size_t)c.sample_keys : ~(size_t)0;
     Rng rng{c.seed};
     std::map<Genome, float> cache;
-    Genome champion{EVOSORT_ALGO_RADIX, 8, w == 4 ? 2 : 3, 3, 32};
+    Genome champion = default_genome(w);
     float champion_f = INFINITY;
     auto fitness = [&](const Genome& g0) -> float {
-        const Genome g = g0.canon();
+        const Genome g = g0.canon(c.mode, n, w);
         auto it = cache.find(g);
         if (it != cache.end()) return it->second;
         evosort_params p;
-        to_params(g0, &p, nullptr);
+        to_params(g0, w, &p, nullptr);
         float f = fitness_cb(&p, std::isfinite(champion_f) ? champion_f : -1.f, ctx);
         if (!(f >= 0.f)) f = INFINITY;   // negative or NaN: failed genome
         cache[g] = f;
         return f;
     };
+    auto restrict_genes = [&](Genome& g) {
+        if (!c.allow_merge) g.algo = EVOSORT_ALGO_RADIX;
+    };
     // initial population (the paper draws T_insertion from [2, 256] first)
     std::vector<Genome> pop(c.population);
     for (auto& g : pop) {
         g = random_genome(rng, c.tins_init_max);
-        if (!c.allow_merge) g.algo = EVOSORT_ALGO_RADIX;
+        restrict_genes(g);
     }
     // seed the defaults so the tuned result is never worse than the plain path
-    pop[0] = Genome{EVOSORT_ALGO_RADIX, 8, w == 4 ? 2 : 3, 4, 32};
+    pop[0] = default_genome(w);
     std::vector<float> fit(c.population);
     for (int gen = 0; gen < c.generations; ++gen) {
         for (int i = 0; i < c.population; ++i) {
@@ -251,7 +331,7 @@ evosort_status evosort_ga_search(const evosort_ga_config* cfg, int key_bytes, ev
             log[gen].mean_ms = nfin ? sum / nfin : INFINITY;
             log[gen].worst_ms = nfin ? worst : INFINITY;
             log[gen].evaluations = (int)cache.size();
-            to_params(pop[idx[0]], &log[gen].best, nullptr);
+            to_params(pop[idx[0]].canon(c.mode, n, w), w, &log[gen].best, nullptr);
         }
         if (gen == c.generations - 1) break;
         // next generation: elites, then tournament-selected parents with
@@ -269,22 +349,26 @@ evosort_status evosort_ga_search(const evosort_ga_config* cfg, int key_bytes, ev
         while ((int)next.size() < c.population) {
             Genome a = select(), b = select();
             if (rng.unit() < c.crossover_p) {
-                if (rng.unit() < 0.5) std::swap(a.algo, b.algo);
-                if (rng.unit() < 0.5) std::swap(a.d, b.d);
-                if (rng.unit() < 0.5) std::swap(a.shape, b.shape);
-                if (rng.unit() < 0.5) std::swap(a.rank, b.rank);
-                if (rng.unit() < 0.5) std::swap(a.tins, b.tins);
+                // uniform crossover: each gene from either parent
+                int* ga[] = {&a.algo, &a.d, &a.kern, &a.shape, &a.rank, &a.tins, &a.alater, &a.afirst, &a.small,
+                             &a.sblock, &a.swarp, &a.sgiant};
+                int* gb[] = {&b.algo, &b.d, &b.kern, &b.shape, &b.rank, &b.tins, &b.alater, &b.afirst, &b.small,
+                             &b.sblock, &b.swarp, &b.sgiant};
+                for (int k = 0; k < 12; ++k)
+                    if (rng.unit() < 0.5) std::swap(*ga[k], *gb[k]);
             }
             for (Genome* g : {&a, &b}) {
                 if (rng.unit() < c.mutation_p) {
+                    // uniform mutation: each gene redrawn with gene_mutation_p
                     const Genome r = random_genome(rng, 2048);
-                    if (rng.unit() < c.gene_mutation_p) g->algo = r.algo;
-                    if (rng.unit() < c.gene_mutation_p) g->d = r.d;
-                    if (rng.unit() < c.gene_mutation_p) g->shape = r.shape;
-                    if (rng.unit() < c.gene_mutation_p) g->rank = r.rank;
-                    if (rng.unit() < c.gene_mutation_p) g->tins = r.tins;
+                    int* gg[] = {&g->algo, &g->d, &g->kern, &g->shape, &g->rank, &g->tins, &g->alater, &g->afirst,
+                                 &g->small, &g->sblock, &g->swarp, &g->sgiant};
+                    const int* rr[] = {&r.algo, &r.d, &r.kern, &r.shape, &r.rank, &r.tins, &r.alater, &r.afirst,
+                                       &r.small, &r.sblock, &r.swarp, &r.sgiant};
+                    for (int k = 0; k < 12; ++k)
+                        if (rng.unit() < c.gene_mutation_p) *gg[k] = *rr[k];
                 }
-                if (!c.allow_merge) g->algo = EVOSORT_ALGO_RADIX;
+                restrict_genes(*g);
             }
             next.push_back(a);
             if ((int)next.size() < c.population) next.push_back(b);
@@ -295,7 +379,8 @@ evosort_status evosort_ga_search(const evosort_ga_config* cfg, int key_bytes, ev
         set_error("evosort_ga_search: no genome produced a verified sort");
         return EVOSORT_ERR_CUDA;
     }
-    to_params(champion, best, nullptr);
+    // reported with the genes that had no effect set to the defaults
+    to_params(champion.canon(c.mode, n, w), w, best, nullptr);
     if (best_ms) *best_ms = champion_f;
     return EVOSORT_OK;
 }
@@ -362,6 +447,8 @@ evosort_status evosort_tune(const void* sample, size_t n, evosort_dtype dt, cons
     evosort_ga_config c;
     if (cfg) c = *cfg;
     else evosort_default_ga_config(&c);
+    c.mode = MODE_ARRAY;
+    c.sample_keys = n;
     DeviceFitness F;
     F.sample = sample;
     F.expected = expected;

@@ -3,13 +3,18 @@
 For each distribution class the dispatcher tells apart, the GA runs on a
 seeded sample of a representative workload of that class, on the GPU, and
 the winning parameters go into the table under (dtype, floor(log2 n), class).
-Candidates are verified on the device (sortedness and a multiset fingerprint
-of the input); no CPU code takes part.  The paper tunes per array size with a
-population of 30 over 10 generations (Section 4.2); so does this script, per
-class as well.
+Every candidate's output is compared bit for bit with a reference sort of the
+same sample made once before the search by a different kernel (the staged
+radix tile with fixed parameters); no CPU code takes part.  The paper tunes
+per array size with a population of 30 over 10 generations (Section 4.2); so
+does this script, per class as well.  With --mode segmented the GA tunes the
+batched segmented sort's tier cut-overs on a batch of log-uniform segment
+lengths and stores them under the 'segmented' class.
 
     python -m paper_2505_18681_gb300.tune --dtype int64 --n 268435456 \\
         --out paper_2505_18681_gb300/tuned/gb300_int64.txt
+    python -m paper_2505_18681_gb300.tune --mode segmented --dtype int32 --segments 10000 \\
+        --out paper_2505_18681_gb300/tuned/gb300_int32.txt
 """
 from __future__ import annotations
 
@@ -69,8 +74,15 @@ def tune_table(dtype=torch.int64, n=1 << 28, classes=None, seed=42, population=3
         got = evo.classify(x)
         # the table's current entry for this class (or the built-in defaults)
         incumbent, _ = evo.plan(x)
+        # the reference every candidate must equal: the staged tile, fixed
+        # parameters (a kernel the search mostly does not use)
+        ref = torch.empty_like(x)
+        evo.sort(x, out=ref, algo="radix", pass_kernel=1, rank_mode=3, digit_bits=8, small_cap=1)
+        evo.sync()
         t0 = time.time()
-        best, ms, log = evo.tune(x, population=population, generations=generations, reps=reps, seed=seed)
+        best, ms, log = evo.tune(x, expected=ref, population=population, generations=generations, reps=reps,
+                                 seed=seed)
+        del ref
         dt = time.time() - t0
         # a search can miss a corner the previous one found: both are timed
         # the same way and the faster one is kept
@@ -97,6 +109,58 @@ def tune_table(dtype=torch.int64, n=1 << 28, classes=None, seed=42, population=3
     return results
 
 
+def tune_segmented(dtype=torch.int32, nseg=10_000, lo=16, hi=1_000_000, seed=42, population=30, generations=10,
+                   reps=3, verbose=True):
+    """GA over the segmented sort's tier cut-overs (warp tier, block tier,
+    giant segments) and the block tier's insertion threshold, on a batch of
+    nseg segments with log-uniform lengths lo..hi (half uniform, half nearly
+    sorted keys).  Fitness: the median device time of the batched sort; a
+    candidate whose output differs from the reference batch sort (made once
+    with the built-in cut-overs) fails."""
+    import paper_2505_18681_gb300 as evo
+    lens = inputs.segment_lengths(nseg, lo, hi, seed=seed)
+    keys, offs = inputs.segmented_keys(lens, dtype, seed=seed, device="cuda")
+    d_offs = offs.to("cuda")
+    total = keys.numel()
+    ref = keys.clone()
+    evo.segmented_sort(ref, d_offs, algo="radix")
+    evo.sync()
+    work = torch.empty_like(keys)
+    s = torch.cuda.current_stream()
+
+    def fitness(p, _best):
+        params = evo.make_params(stream=s, **p)
+        ts = []
+        for _ in range(max(reps, 1)):
+            work.copy_(keys)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            try:
+                evo.segmented_sort(work, d_offs, params=params)
+            except evo.EvoSortError:
+                return -1.0
+            e1.record(s)
+            try:
+                evo.sync(s)
+            except evo.EvoSortError:
+                return -1.0
+            ts.append(e0.elapsed_time(e1))
+            if not torch.equal(work, ref):
+                return -1.0
+        ts.sort()
+        return ts[len(ts) // 2]
+
+    t0 = time.time()
+    best, ms, log = evo.ga_search(fitness, key_bytes=keys.element_size(), mode=1, population=population,
+                                  generations=generations, seed=seed)
+    evo.table_set(dtype, bucket(total), "segmented", best, ms)
+    if verbose:
+        print("segmented %d segments, %d keys: best %.3f ms %s (%.0f s)" % (nseg, total, ms, best,
+                                                                             time.time() - t0), flush=True)
+    return {"segments": nseg, "total": total, "best": best, "best_ms": ms, "log": log,
+            "defaults_ms": log[0]["best_ms"] if log else None}
+
+
 def main():
     import paper_2505_18681_gb300 as evo
     ap = argparse.ArgumentParser()
@@ -109,12 +173,21 @@ def main():
     ap.add_argument("--seed", type=int, default=42)
     ap.add_argument("--out", required=True)
     ap.add_argument("--log", default=None)
+    ap.add_argument("--mode", default="array", choices=["array", "segmented"])
+    ap.add_argument("--segments", type=int, default=10_000)
     a = ap.parse_args()
     evo.library()
     if os.path.exists(a.out):
         evo.table_load(a.out)
-    tune_table(getattr(torch, a.dtype), a.n, a.classes.split(","), a.seed, a.population, a.generations, a.reps,
-               a.log)
+    if a.mode == "segmented":
+        res = tune_segmented(getattr(torch, a.dtype), a.segments, seed=a.seed, population=a.population,
+                             generations=a.generations, reps=a.reps)
+        if a.log:
+            with open(a.log, "w") as f:
+                json.dump(res, f, indent=1)
+    else:
+        tune_table(getattr(torch, a.dtype), a.n, a.classes.split(","), a.seed, a.population, a.generations,
+                   a.reps, a.log)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     evo.table_save(a.out)
 

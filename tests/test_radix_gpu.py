@@ -376,3 +376,42 @@ def test_cuda_graph_capture_of_a_device_wide_sort(evo, algo):
         g.replay()
         torch.cuda.synchronize()
         assert np.array_equal(bits(y), oracle.radix_sort(x.cpu().numpy()).view(np.uint64))
+
+
+@pytest.mark.parametrize("pass_kernel", [1, 2])
+def test_lookback_wait_times_out_and_recovers(evo, pass_kernel):
+    """With the look-back poll limit cut to one poll, a multi-tile sort's
+    waits run out: the kernels return, evosort_sync reports ERR_TIMEOUT, and
+    the next sort with the default limit matches the oracle (the context
+    stays usable).  No wait is left unbounded: every other wait keeps its
+    limit, and the per-digit range check keeps stores inside the array."""
+    x = gen("uniform", 12_000_017, torch.int32, seed=5)
+    y = torch.empty_like(x)
+    evo.sync()
+    evo.set_wait_limit(1)
+    try:
+        evo.sort(x, out=y, algo="radix", pass_kernel=pass_kernel, rank_mode=3)
+        with pytest.raises(evo.EvoSortError) as ei:
+            evo.sync()
+        assert ei.value.status == "ERR_TIMEOUT"
+    finally:
+        evo.set_wait_limit(0)
+    evo.sync()   # the status word was cleared when it was reported
+    run_keys(evo, x, algo="radix", pass_kernel=pass_kernel)
+
+
+def test_adaptive_thresholds_are_parameters(evo):
+    """adapt_later=10 (1/1024) sends every pass after the first that runs to
+    match.any; adapt_first=1 (1/2) keeps the first on match masks; the result
+    is the oracle's."""
+    x = gen("uniform", ADAPT_N, torch.int64, seed=9)
+    y = torch.empty_like(x)
+    evo.profile(True)
+    try:
+        evo.sort(x, out=y, algo="radix", rank_mode=4, adapt_later=10, adapt_first=1)
+        evo.sync()
+        recs = [r for r in evo.profile_read() if r["kind"] == "radix_onesweep" and r["active"]]
+    finally:
+        evo.profile(False)
+    assert {r["pass"]: r["rank"] for r in recs} == {0: 3, 1: 1, 2: 1, 3: 1, 4: 1, 5: 1, 6: 1, 7: 1}
+    assert np.array_equal(bits(y), oracle.radix_sort(x.cpu().numpy()).view(np.uint64))

@@ -139,3 +139,69 @@ def test_cuda_graph_capture_and_replay(evo):
         torch.cuda.synchronize()
         expect = oracle.segmented_sort(fresh.cpu().numpy(), offs.numpy().astype(np.uint64))
         assert np.array_equal(bits(work), bits(expect))
+
+
+@pytest.mark.parametrize("cap", [32, 64, 128, 256])
+def test_warp_tier_cut_over(evo, cap):
+    """Every warp-tier cut-over: lengths around each power of two go to the
+    warp or the block tier; the result is the oracle's either way."""
+    lengths = [0, 1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 600, 5000]
+    run(evo, lengths, torch.int32, seg_warp_cap=cap)
+    run(evo, lengths, torch.float64, seg_warp_cap=cap)
+
+
+def test_giant_segment_takes_the_device_wide_path(evo):
+    """One 5e7-key segment among 10,000 small ones: the giant segment is
+    sorted by the device-wide radix path (its onesweep launches appear),
+    the rest by the persistent launch; every segment matches the oracle."""
+    from paper_2505_18681_gb300 import inputs
+    small = inputs.segment_lengths(10_000, 16, 5_000, seed=8).tolist()
+    lengths = list(small[:5000]) + [50_000_000] + list(small[5000:])
+    keys, offs = make(lengths, torch.int32, seed=9)
+    expect = oracle.segmented_sort(keys.cpu().numpy(), offs.numpy().astype(np.uint64))
+    d_offs = offs.to("cuda")
+    evo.profile(True)
+    try:
+        evo.segmented_sort(keys, d_offs)
+        evo.sync()
+        kinds = [r["kind"] for r in evo.profile_read()]
+    finally:
+        evo.profile(False)
+    assert "radix_onesweep" in kinds and "segmented" in kinds
+    assert np.array_equal(bits(keys), bits(expect))
+
+
+def test_giant_tier_off_and_under_capture(evo):
+    """seg_giant=-1 keeps every segment in the persistent launch; a captured
+    batch (no host read possible) does the same; both match the oracle."""
+    lengths = [2_000_000, 300, 70_000, 5, 1_100_000]
+    run(evo, lengths, torch.int64, seg_giant=-1)
+    run(evo, lengths, torch.int64, seg_giant=1 << 20)
+    keys, offs = make(lengths, torch.int64, seed=4)
+    expect = oracle.segmented_sort(keys.cpu().numpy(), offs.numpy().astype(np.uint64))
+    d_offs = offs.to("cuda")
+    work = keys.clone()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        evo.segmented_sort(work, d_offs, seg_giant=1 << 20, stream=s)   # warm-up outside capture
+        evo.sync(s)
+        g = torch.cuda.CUDAGraph()
+        work.copy_(keys)
+        with torch.cuda.graph(g, stream=s):
+            evo.segmented_sort(work, d_offs, seg_giant=1 << 20, stream=s)
+    work.copy_(keys)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(work), bits(expect))
+
+
+def test_segmented_table_entry_is_used(evo):
+    """A tuned entry for segmented batches (class 'segmented') is taken when
+    the caller leaves the choice open; the result is the oracle's."""
+    evo.table_clear()
+    try:
+        evo.table_set(torch.int32, 20, "segmented", {"algo": 0, "seg_block_cap": 1024, "seg_warp_cap": 64,
+                                                     "seg_giant": -1, "insertion_threshold": 8})
+        run(evo, [10, 70, 300, 2000, 9000, 40_000, 1_000_000], torch.int32)
+    finally:
+        evo.table_clear()

@@ -95,3 +95,93 @@ def test_dispatcher_uses_table(evo):
     evo.table_clear()
     p, cls = evo.plan(x)                      # empty table: defaults, no sampling
     assert p["algo"] == 0 and p["digit_bits"] == 0
+
+
+TUNED = ["gb300_int32.txt", "gb300_int64.txt"]
+
+
+def table_lines(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2505_18681_gb300",
+                        "tuned", name)
+    out = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            out.append([float(t) if "." in t else int(t) for t in line.split()])
+    return out
+
+
+def line_params(f):
+    names = ["algo", "digit_bits", "block_size", "keys_per_thread", "rank_mode", "insertion_threshold",
+             "seg_block_cap"]
+    p = dict(zip(names, f[3:10]))
+    extra = ["pass_kernel", "adapt_later", "adapt_first", "seg_warp_cap", "small_cap", "seg_giant"]
+    p.update(zip(extra, f[11:17]))
+    return p
+
+
+@pytest.mark.parametrize("name", TUNED)
+def test_every_tuned_table_line_matches_the_oracle(evo, name):
+    """Each committed table entry, run with exactly its parameters on its
+    class's representative workload (the workload it was tuned on, at a size
+    the oracle sorts quickly), gives the oracle's answer bit for bit; the
+    segmented entry runs on a batch of the tuned shape."""
+    from paper_2505_18681_gb300 import inputs
+    from paper_2505_18681_gb300.tune import REPRESENTATIVE
+    classes = {v: k for k, v in evo.CLASSES.items()}
+    dtype = torch.int32 if "int32" in name else torch.int64
+    lines = table_lines(name)
+    assert lines, name
+    for f in lines:
+        cls = evo.CLASSES[f[2]]
+        p = line_params(f)
+        if cls == "segmented":
+            lens = inputs.segment_lengths(2_000, 16, 100_000, seed=6)
+            keys, offs = inputs.segmented_keys(lens, dtype, seed=6, device="cuda")
+            expect = oracle.segmented_sort(keys.cpu().numpy(), offs.numpy().astype(np.uint64))
+            evo.segmented_sort(keys, offs.to("cuda"), **p)
+            evo.sync()
+            assert np.array_equal(keys.cpu().numpy(), expect), (name, f)
+            continue
+        assert cls in classes
+        for n in (1 << 20, 3_000_017):
+            x = inputs.generate(REPRESENTATIVE[cls], n, dtype, seed=42, device="cuda")
+            y = torch.empty_like(x)
+            evo.sort(x, out=y, **p)
+            evo.sync()
+            assert np.array_equal(y.cpu().numpy(), oracle.radix_sort(x.cpu().numpy())), (name, f, n)
+
+
+def test_segmented_tuning_against_the_oracle(evo):
+    """The GA in its segmented mode (tier cut-overs and the block tier's
+    insertion threshold) with a device-timed fitness whose every candidate
+    is checked against the oracle's per-segment sort."""
+    from paper_2505_18681_gb300 import inputs
+    lens = inputs.segment_lengths(3_000, 16, 60_000, seed=3)
+    keys, offs = inputs.segmented_keys(lens, torch.int32, seed=3, device="cuda")
+    expect = torch.from_numpy(oracle.segmented_sort(keys.cpu().numpy(), offs.numpy().astype(np.uint64))).cuda()
+    d_offs = offs.to("cuda")
+    work = torch.empty_like(keys)
+    seen = []
+
+    def fitness(p, _best):
+        work.copy_(keys)
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        try:
+            evo.segmented_sort(work, d_offs, params=evo.make_params(**p))
+        except evo.EvoSortError:
+            return -1.0
+        e1.record(s)
+        evo.sync()
+        seen.append(p)
+        return e0.elapsed_time(e1) if torch.equal(work, expect) else -1.0
+
+    best, ms, log = evo.ga_search(fitness, key_bytes=4, mode=1, population=10, generations=3, seed=4)
+    assert np.isfinite(ms) and ms > 0 and len(log) == 3
+    assert len({(q["seg_block_cap"], q["seg_warp_cap"], q["seg_giant"]) for q in seen}) > 1
+    work.copy_(keys)
+    evo.segmented_sort(work, d_offs, params=evo.make_params(**best))
+    evo.sync()
+    assert torch.equal(work, expect)
