@@ -590,15 +590,25 @@ def leg_floatpairs(evo, args, stream, barrier, dev):
             "gpu_launches": launches}
 
 
-def leg_segmented(evo, args, stream, barrier, dev, nseg=100_000):
+def leg_segmented(evo, args, stream, barrier, dev, nseg=100_000, rank=0, world=1):
     """100,000 int32 arrays with log-uniform lengths 16..1e6 (half uniform,
     half nearly sorted): one batched call with the GA-tuned cut-overs against
-    the built-in ones and against one sort call per array."""
+    the built-in ones and against one sort call per array.  With world > 1
+    ranks the batch is sharded by whole segments (longest first, to the rank
+    with the fewest keys): each rank generates and sorts only its own share,
+    nothing is exchanged, and the value is all keys over the slowest rank's
+    time (strong scaling)."""
     import torch
-    from paper_2505_18681_gb300 import inputs
+    from paper_2505_18681_gb300 import inputs, shard
     lens = inputs.segment_lengths(nseg, 16, 1_000_000, seed=42)
-    keys, offs = inputs.segmented_keys(lens, torch.int32, seed=42, device=dev)
+    loads = None
+    if world > 1:
+        owned, loads = shard.partition_segments(lens, world)
+        keys, offs = shard.rank_batch(lens, owned[rank], torch.int32, seed=42, device=dev)
+    else:
+        keys, offs = inputs.segmented_keys(lens, torch.int32, seed=42, device=dev)
     d_offs = offs.to(dev)
+    total_all = int(lens.sum())
     total = keys.numel()
     work = torch.empty_like(keys)
     evo.table_clear()
@@ -612,8 +622,18 @@ def leg_segmented(evo, args, stream, barrier, dev, nseg=100_000):
             work.copy_(keys)
             evo.segmented_sort(work, d_offs, params=p)
         return f
+    barrier()
     ms_t, recs, clocks, launches = _timed_with_profile(evo, batched(tuned), args.steps, args.warmup, stream)
-    ms_t -= copy_ms
+    barrier()
+    ms_t = max_over_ranks(ms_t - copy_ms, dev)
+    if world > 1:
+        evo.table_clear()
+        return {"value": total_all / (ms_t * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": ms_t, "dtype": "i32",
+                "n_gpus": world, "scaling": "strong",
+                "config": {"workload": "batched segmented sort: %d int32 arrays, log-uniform lengths 16..1e6, %d "
+                           "keys total, sharded over %d ranks by whole segments (no exchange)"
+                           % (nseg, total_all, world), "keys_per_rank": loads},
+                "kernel_time_share": kernel_shares(recs), "clocks": clocks}
     ms_d = _time_steps(batched(defaults), args.steps, 1, stream) - copy_ms
     # one sort call per array with the library's own choice (no table: the
     # one-CTA path for short arrays, the device-wide radix sort for the rest)
@@ -750,9 +770,26 @@ def other_workload(args):
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     line = {"metric": METRIC, "unit": "GKeys/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
-    if args.workload in ("floatpairs", "segmented", "u32big", "small", "merge", "int32"):
-        leg = {"floatpairs": leg_floatpairs, "segmented": lambda *a: leg_segmented(*a, nseg=args.segments),
-               "u32big": leg_u32big, "small": leg_small, "merge": leg_merge, "int32": leg_int32}[args.workload]
+    if args.workload == "segmented":
+        # one rank per GPU under torchrun: each sorts its own share of the batch
+        import torch.distributed as tdist
+        ws, rank, local = dist_env()
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        if ws > 1:
+            tdist.init_process_group("nccl", device_id=dev)
+        res = leg_segmented(evo, args, torch.cuda.current_stream(), (lambda: tdist.barrier()) if ws > 1 else
+                            (lambda: None), dev, nseg=args.segments, rank=rank, world=ws)
+        if rank == 0:
+            line.update(res)
+            line["n_gpus"] = ws
+            print(json.dumps(line), flush=True)
+        if ws > 1:
+            tdist.destroy_process_group()
+        return
+    if args.workload in ("floatpairs", "u32big", "small", "merge", "int32"):
+        leg = {"floatpairs": leg_floatpairs, "u32big": leg_u32big, "small": leg_small, "merge": leg_merge,
+               "int32": leg_int32}[args.workload]
         line.update(leg(evo, args, stream, lambda: None, torch.device("cuda")))
         print(json.dumps(line), flush=True)
         return

@@ -170,7 +170,7 @@ static RadixLayout radix_layout(size_t n, int w, bool pairs, const Plan& pl) {
     L.off_desc = off;
     off = align_up(off + (L.npass + 1) * sizeof(PassDesc), 256);
     L.off_tiles = off;
-    off = align_up(off + L.npass * sizeof(uint32_t), 256);
+    off = align_up(off + (L.npass + 4) * sizeof(uint32_t), 256);   // tile counters, then the order flags
     L.off_counts = off;
     off = align_up(off + L.npass * bins * sizeof(unsigned long long), 256);
     L.off_lookback = off;
@@ -226,6 +226,7 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     a.counts = (unsigned long long*)(base + L.off_counts);
     a.lookback = base + L.off_lookback;
     a.tile_counter = (uint32_t*)(base + L.off_tiles);
+    a.order = a.tile_counter + L.npass;
     a.status = status;
     const int inplace = (in == out) ? 1 : 0;
 

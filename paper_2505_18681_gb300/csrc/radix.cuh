@@ -26,7 +26,12 @@ namespace evosort {
 
 // Buffer selectors of the pass chain.
 enum : int { BUF_IN = 0, BUF_OUT = 1, BUF_TMP = 2 };
-enum : int { FIX_NONE = 0, FIX_IN_TO_OUT = 1, FIX_TMP_TO_OUT = 2 };
+enum : int { FIX_NONE = 0, FIX_IN_TO_OUT = 1, FIX_TMP_TO_OUT = 2, FIX_REVERSE = 3 };
+
+// Order flags K1 records while it counts (words of RadixArgs::order): a pair
+// of neighbours that descends, that ascends, that is equal (in the order the
+// sort produces, i.e. on the mapped keys).
+enum : int { ORD_DESCENT = 0, ORD_ASCENT = 1, ORD_EQUAL = 2 };
 
 struct PassDesc {
     int active;   // 0: the digit is constant over all keys, pass skipped
@@ -59,6 +64,7 @@ struct RadixArgs {
     unsigned long long* counts; // npass << d digit counts, then exclusive offsets
     void* lookback;             // slots [pass][tile][digit]
     uint32_t* tile_counter;     // npass counters
+    uint32_t* order;            // 3 order flags (ORD_*), zeroed with the counters
     uint32_t* status;
 };
 
@@ -86,6 +92,10 @@ __device__ __forceinline__ uint32_t* sel_vdst(const RadixArgs& a, int s) {
 // consecutive keys and merges consecutive equal digits before the atomic;
 // when a whole warp ends its runs on one digit (sorted and low-entropy input)
 // the warp adds one reduced count instead of 32.
+// While it counts, K1 also compares every key with its successor and records
+// whether any pair descends, ascends or is equal (ORD_* flags): K2 then
+// turns an input that is already in order into a copy, and one in exactly
+// reverse order into a reversed copy, instead of running the passes.
 // ---------------------------------------------------------------------------
 constexpr int kHistThreads = 1024;
 constexpr size_t kHistSmem = 128 * 1024;
@@ -136,13 +146,20 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
     const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t gthreads = (size_t)gridDim.x * blockDim.x;
 
-    auto count_key = [&](U k) {
-        k = map_fwd(k, map);
+    bool dsc = false, asc = false, eq = false;   // order relations seen by this thread
+    auto relate = [&](U x, U y) {   // x precedes y in memory (both mapped)
+        dsc |= x > y;
+        asc |= x < y;
+        eq |= x == y;
+    };
+    auto count_key = [&](size_t i) {
+        const U k = map_fwd(keys[i], map);
         for (int p = 0; p < a.npass; ++p)
             atomicAdd(&s_h[(p * bins + digit_of(k, p * a.d, mask)) * cols + col], 1u);
+        if (i + 1 < n) relate(k, map_fwd(keys[i + 1], map));
     };
-    if (gtid < head) count_key(keys[gtid]);
-    if (gtid < n - tail0) count_key(keys[tail0 + gtid]);
+    if (gtid < head) count_key(gtid);
+    if (gtid < n - tail0) count_key(tail0 + gtid);
 
     // warps take 32 runs (32 * HC consecutive keys) at a time; lane L reads
     // the 16-byte vectors L, L + 32, ... of the warp's chunk, so every load
@@ -161,6 +178,24 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
             }
 #pragma unroll
             for (int j = 0; j < HC; ++j) k[j] = map_fwd(k[j], map);
+            // neighbours: inside a vector (this thread), from one vector to the
+            // next (the next lane, or lane 0's next vector for lane 31), and
+            // from the chunk's last key to the next key in memory
+#pragma unroll
+            for (int j = 0; j < HC / V; ++j) {
+#pragma unroll
+                for (int t = 0; t + 1 < V; ++t) relate(k[j * V + t], k[j * V + t + 1]);
+                const U nx = __shfl_down_sync(0xffffffffu, k[j * V], 1);
+                const U nx0 = __shfl_sync(0xffffffffu, k[(j + 1 < HC / V ? j + 1 : j) * V], 0);
+                if (lane < 31) {
+                    relate(k[j * V + V - 1], nx);
+                } else if (j + 1 < HC / V) {
+                    relate(k[j * V + V - 1], nx0);
+                } else {
+                    const size_t after = head + (c + 1) * 32 * HC;   // first key after this chunk
+                    if (after < n) relate(k[j * V + V - 1], map_fwd(keys[after], map));
+                }
+            }
             for (int p = 0; p < a.npass; ++p) {
                 const int sh = p * a.d;
                 uint32_t* h = s_h + (size_t)p * bins * cols;
@@ -181,10 +216,102 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
             }
         }
     }
+    if (__any_sync(0xffffffffu, dsc) && lane == 0) atomicOr(&a.order[ORD_DESCENT], 1u);
+    if (__any_sync(0xffffffffu, asc) && lane == 0) atomicOr(&a.order[ORD_ASCENT], 1u);
+    if (__any_sync(0xffffffffu, eq) && lane == 0) atomicOr(&a.order[ORD_EQUAL], 1u);
     __syncthreads();
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
         uint32_t sum = 0;
         for (int c = 0; c < cols; ++c) sum += s_h[i * cols + ((c + i) & (cols - 1))];
+        if (sum) atomicAdd(&a.counts[i], (unsigned long long)sum);
+    }
+}
+
+// K1 for 8-bit digits (the default): the pass count and every digit's shift
+// are compile-time constants, and each key adds one to its lane's column of
+// each pass's counters directly (no run merging: the columns already keep a
+// warp's atomics apart, and merging costs a compare per digit on random
+// keys).  Counters of 64-bit keys use 16 columns (2 lanes per column) to fit
+// 128 KB.  The order relations are recorded as in the generic kernel.
+template <typename U>
+__global__ void __launch_bounds__(kHistThreads) radix_histogram8(RadixArgs a) {
+    extern __shared__ uint32_t s_h[];
+    constexpr int NP = (int)sizeof(U);
+    constexpr int BINS = 256;
+    constexpr int COLS = hist_cols(NP, 8);
+    for (int i = threadIdx.x; i < NP * BINS * COLS; i += blockDim.x) s_h[i] = 0;
+    __syncthreads();
+
+    constexpr int V = 16 / sizeof(U);
+    constexpr int HC = 64 / sizeof(U);   // keys per thread per chunk (16 registers of keys)
+    const U* keys = (const U*)a.in;
+    const size_t n = a.n;
+    const KeyMap map = a.map;
+    const int lane = threadIdx.x & 31;
+    uint32_t* hcol = s_h + (lane & (COLS - 1));
+    size_t head = ((16 - ((uintptr_t)keys & 15)) & 15) / sizeof(U);
+    if (head > n) head = n;
+    const size_t nchunks = (n - head) / (32 * HC);
+    const size_t tail0 = head + nchunks * 32 * HC;
+    const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t gthreads = (size_t)gridDim.x * blockDim.x;
+
+    auto add = [&](U k) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+            atomicAdd(&hcol[(p * BINS + (uint32_t)((k >> (8 * p)) & 0xFFu)) * COLS], 1u);
+    };
+    bool dsc = false, asc = false, eq = false;
+    auto relate = [&](U x, U y) {
+        dsc |= x > y;
+        asc |= x < y;
+        eq |= x == y;
+    };
+    auto count_key = [&](size_t i) {
+        const U k = map_fwd(keys[i], map);
+        add(k);
+        if (i + 1 < n) relate(k, map_fwd(keys[i + 1], map));
+    };
+    if (gtid < head) count_key(gtid);
+    if (gtid < n - tail0) count_key(tail0 + gtid);
+
+    const size_t warp_id = gtid >> 5;
+    const size_t nwarps = gthreads >> 5;
+    for (size_t c = warp_id; c < nchunks; c += nwarps) {
+        U k[HC];
+        const uint4* vp = (const uint4*)(keys + head + c * 32 * HC);
+#pragma unroll
+        for (int j = 0; j < HC / V; ++j) {
+            const uint4 v = __ldcs(vp + j * 32 + lane);
+            memcpy(&k[j * V], &v, 16);
+        }
+#pragma unroll
+        for (int j = 0; j < HC; ++j) k[j] = map_fwd(k[j], map);
+#pragma unroll
+        for (int j = 0; j < HC / V; ++j) {
+#pragma unroll
+            for (int t = 0; t + 1 < V; ++t) relate(k[j * V + t], k[j * V + t + 1]);
+            const U nx = __shfl_down_sync(0xffffffffu, k[j * V], 1);
+            const U nx0 = __shfl_sync(0xffffffffu, k[(j + 1 < HC / V ? j + 1 : j) * V], 0);
+            if (lane < 31) {
+                relate(k[j * V + V - 1], nx);
+            } else if (j + 1 < HC / V) {
+                relate(k[j * V + V - 1], nx0);
+            } else {
+                const size_t after = head + (c + 1) * 32 * HC;
+                if (after < n) relate(k[j * V + V - 1], map_fwd(keys[after], map));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < HC; ++j) add(k[j]);
+    }
+    if (__any_sync(0xffffffffu, dsc) && lane == 0) atomicOr(&a.order[ORD_DESCENT], 1u);
+    if (__any_sync(0xffffffffu, asc) && lane == 0) atomicOr(&a.order[ORD_ASCENT], 1u);
+    if (__any_sync(0xffffffffu, eq) && lane == 0) atomicOr(&a.order[ORD_EQUAL], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < NP * BINS; i += blockDim.x) {
+        uint32_t sum = 0;
+        for (int c = 0; c < COLS; ++c) sum += s_h[i * COLS + ((c + i) & (COLS - 1))];
         if (sum) atomicAdd(&a.counts[i], (unsigned long long)sum);
     }
 }
@@ -244,6 +371,19 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
     if (threadIdx.x == 0) {
         int active[64];
         int e = 0;
+        // already in order: no pass runs, the input is copied (or, in place,
+        // left as it is); in exactly reverse order (for key/value sorts with
+        // no two equal keys, so the result stays stable): a reversed copy
+        const bool in_order = a.order[ORD_DESCENT] == 0;
+        const bool reversed = !in_order && a.order[ORD_ASCENT] == 0 && (!a.vout || a.order[ORD_EQUAL] == 0);
+        if (in_order || reversed) {
+            for (int p = 0; p <= a.npass; ++p) {
+                PassDesc z = {};
+                a.desc[p] = z;
+            }
+            a.desc[a.npass].fixup = reversed ? FIX_REVERSE : (inplace ? FIX_NONE : FIX_IN_TO_OUT);
+            return;
+        }
         for (int p = 0; p < a.npass; ++p)
             if (!s_trivial[p]) active[e++] = p;
         for (int p = 0; p <= a.npass; ++p) {
@@ -776,18 +916,71 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
 // ---------------------------------------------------------------------------
 // K3b: result copy when the pass chain did not end in the output buffer.
 // ---------------------------------------------------------------------------
+// Copies in 16-byte vectors where both sides are aligned; the reversed copy
+// reads each vector's keys with coalesced scalar loads (descending addresses)
+// and stores them as one vector.
+template <typename T>
+__device__ __forceinline__ void copy_forward(const T* s, T* o, size_t n, size_t t0, size_t stride) {
+    constexpr int V = 16 / sizeof(T);
+    if (((uintptr_t)s & 15) == 0 && ((uintptr_t)o & 15) == 0) {
+        const size_t nv = n / V;
+        for (size_t q = t0; q < nv; q += stride) __stcs((uint4*)o + q, __ldcs((const uint4*)s + q));
+        for (size_t i = nv * V + t0; i < n; i += stride) o[i] = s[i];
+    } else {
+        for (size_t i = t0; i < n; i += stride) o[i] = s[i];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_reversed(const T* s, T* o, size_t n, size_t t0, size_t stride) {
+    constexpr int V = 16 / sizeof(T);
+    if (((uintptr_t)o & 15) == 0) {
+        const size_t nv = n / V;
+        for (size_t q = t0; q < nv; q += stride) {
+            T v[V];
+#pragma unroll
+            for (int t = 0; t < V; ++t) v[t] = __ldcs(s + (n - 1 - (q * V + t)));
+            uint4 u;
+            memcpy(&u, v, 16);
+            __stcs((uint4*)o + q, u);
+        }
+        for (size_t i = nv * V + t0; i < n; i += stride) o[i] = s[n - 1 - i];
+    } else {
+        for (size_t i = t0; i < n; i += stride) o[i] = s[n - 1 - i];
+    }
+}
+
 template <typename U>
 __global__ void __launch_bounds__(256) radix_fixup(RadixArgs a) {
     const int fix = a.desc[a.npass].fixup;
     if (fix == FIX_NONE) return;
-    const U* s = fix == FIX_IN_TO_OUT ? (const U*)a.in : (const U*)a.tmp;
-    const uint32_t* vs = fix == FIX_IN_TO_OUT ? a.vin : a.vtmp;
     U* o = (U*)a.out;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        o[i] = s[i];
-        if (a.vout) a.vout[i] = vs[i];
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n = a.n;
+    if (fix == FIX_REVERSE) {
+        const U* s = (const U*)a.in;
+        if ((const void*)s == (const void*)o) {   // in place: swap mirror pairs
+            for (size_t i = t0; i < n / 2; i += stride) {
+                const U x = o[i];
+                o[i] = o[n - 1 - i];
+                o[n - 1 - i] = x;
+                if (a.vout) {
+                    const uint32_t v = a.vout[i];
+                    a.vout[i] = a.vout[n - 1 - i];
+                    a.vout[n - 1 - i] = v;
+                }
+            }
+        } else {
+            copy_reversed(s, o, n, t0, stride);
+            if (a.vout) copy_reversed(a.vin, a.vout, n, t0, stride);
+        }
+        return;
     }
+    const U* s = fix == FIX_IN_TO_OUT ? (const U*)a.in : (const U*)a.tmp;
+    const uint32_t* vs = fix == FIX_IN_TO_OUT ? a.vin : a.vtmp;
+    copy_forward(s, o, n, t0, stride);
+    if (a.vout) copy_forward(vs, a.vout, n, t0, stride);
 }
 
 }  // namespace evosort

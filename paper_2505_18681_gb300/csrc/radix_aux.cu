@@ -26,11 +26,19 @@ cudaError_t launch_radix_aux(int w, int which, size_t grid, size_t smem, cudaStr
                                  (int)kHistSmem);
             cudaFuncSetAttribute(radix_histogram<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kHistSmem);
+            cudaFuncSetAttribute(radix_histogram8<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHistSmem);
+            cudaFuncSetAttribute(radix_histogram8<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHistSmem);
             configured = true;
         }
         (void)smem;
         const size_t hs = (size_t)a.npass * ((size_t)1 << a.d) * hist_cols(a.npass, a.d) * 4;
-        if (w == 4)
+        if (a.d == 8 && w == 4)
+            radix_histogram8<uint32_t><<<(unsigned)grid, kHistThreads, hs, s>>>(a);
+        else if (a.d == 8)
+            radix_histogram8<uint64_t><<<(unsigned)grid, kHistThreads, hs, s>>>(a);
+        else if (w == 4)
             radix_histogram<uint32_t><<<(unsigned)grid, kHistThreads, hs, s>>>(a);
         else
             radix_histogram<uint64_t><<<(unsigned)grid, kHistThreads, hs, s>>>(a);

@@ -346,14 +346,12 @@ def segment_lengths(nseg: int, lo: int = 16, hi: int = 1_000_000, seed: int = 42
     return torch.clamp(torch.floor(ln).to(torch.int64), lo, hi)
 
 
-def segmented_keys(lengths: torch.Tensor, dtype=torch.int32, seed: int = 42, device="cpu"):
-    """Keys for a batched segmented sort: even segments uniform full range, odd
-    segments an ascending ramp with 1% of positions replaced by uniform random
-    values.  Returns (keys, offsets) with offsets as int64 of length nseg+1."""
+def _segmented_fn(lengths: torch.Tensor, dtype, seed: int, device):
+    """Chunk filler of the segmented batch: the key at global position i
+    depends only on i, its segment and its place in the segment."""
     lengths = lengths.to(torch.int64).cpu()
     offsets = torch.zeros(lengths.numel() + 1, dtype=torch.int64)
     offsets[1:] = torch.cumsum(lengths, 0)
-    total = int(offsets[-1])
     bits = _INT_DTYPES[dtype]
     lo = _signed_min(bits, dtype)
     st = stream_state(seed, _STREAM_ID["segkeys"])
@@ -372,4 +370,20 @@ def segmented_keys(lengths: torch.Tensor, dtype=torch.int32, seed: int = 42, dev
         odd = (seg & 1) == 1
         return torch.where(odd & ~replace, ramp, r)
 
-    return _fill(total, dtype, device, fn), offsets
+    return fn, offsets
+
+
+def segmented_keys(lengths: torch.Tensor, dtype=torch.int32, seed: int = 42, device="cpu"):
+    """Keys for a batched segmented sort: even segments uniform full range, odd
+    segments an ascending ramp with 1% of positions replaced by uniform random
+    values.  Returns (keys, offsets) with offsets as int64 of length nseg+1."""
+    fn, offsets = _segmented_fn(lengths, dtype, seed, device)
+    return _fill(int(offsets[-1]), dtype, device, fn), offsets
+
+
+def segmented_keys_range(lengths: torch.Tensor, start: int, stop: int, dtype=torch.int32, seed: int = 42,
+                         device="cpu") -> torch.Tensor:
+    """The keys at global positions [start, stop) of segmented_keys(lengths,
+    dtype, seed), generated without the rest of the batch."""
+    fn, _ = _segmented_fn(lengths, dtype, seed, device)
+    return _fill(stop - start, dtype, device, lambda s, c: fn(start + s, c))

@@ -64,30 +64,69 @@ def evo():
     return evo
 
 
-def test_nine_distributions_1e9_int64_tuned(evo):
-    """Config 2: 1e9 int64 keys under nine distributions, tuned parameters
-    chosen by the dispatcher, as bench.py runs them."""
+NINE = ("uniform", "gaussian", "sorted", "reverse", "nearly_sorted", "distinct16", "zipf", "equal", "uniform1000")
+
+
+def _nine_full_size(evo, dtype, table_name, full_oracle_dist):
+    """The nine 1e9-key arrays through the dispatcher call bench.py times
+    (AUTO parameters, tuned table loaded): order, multiset and sampled order
+    statistics for every distribution, and one distribution compared with the
+    oracle element by element."""
     import os
     from paper_2505_18681_gb300 import inputs
     table = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2505_18681_gb300",
-                         "tuned", "gb300_int64.txt")
+                         "tuned", table_name)
     evo.table_clear()
     evo.table_load(table)
     n = 1_000_000_000
-    y = torch.empty(n, dtype=torch.int64, device="cuda")
+    y = torch.empty(n, dtype=dtype, device="cuda")
     try:
-        for dist in ("uniform", "gaussian", "sorted", "reverse", "nearly_sorted", "distinct16", "zipf", "equal",
-                     "uniform1000"):
-            x = inputs.generate(dist, n, torch.int64, seed=42, device="cuda")
-            pd, _ = evo.plan(x)
-            evo.sort(x, out=y, **pd)
+        for dist in NINE:
+            x = inputs.generate(dist, n, dtype, seed=42, device="cuda")
+            evo.sort(x, out=y)
             evo.sync()
             assert nondecreasing(y), dist
             assert fingerprint(x) == fingerprint(y), dist
             assert order_stats_ok(x, y, [0, 123_456_789, 500_000_000, n - 1]), dist
+            if dist == full_oracle_dist:
+                assert np.array_equal(y.cpu().numpy(), oracle.radix_sort(x.cpu().numpy())), dist
             del x
     finally:
         evo.table_clear()
+
+
+def test_nine_distributions_1e9_int64_tuned(evo):
+    """Config 2: 1e9 int64 keys under nine distributions, as bench.py's
+    headline sorts them; the uniform array against the full oracle."""
+    _nine_full_size(evo, torch.int64, "gb300_int64.txt", "uniform")
+
+
+def test_nine_distributions_1e9_int32_tuned(evo):
+    """Config 1 at full size (the 1e9-key int32 sort the HBM target is set
+    on), under the same nine distributions; the uniform array against the
+    full oracle."""
+    _nine_full_size(evo, torch.int32, "gb300_int32.txt", "uniform")
+
+
+def test_mergesort_1e8_int32_full_oracle(evo):
+    """Algorithm 3 at scale: 1e8 int32 keys by mergesort (insertion threshold
+    32, about 15 global merge rounds), every element against the oracle; and
+    stable pairs at 2e7 keys."""
+    from paper_2505_18681_gb300 import inputs
+    n = 100_000_000
+    x = inputs.generate("uniform", n, torch.int32, seed=0, device="cuda")
+    y = torch.empty_like(x)
+    evo.sort(x, out=y, algo="merge", insertion_threshold=32)
+    evo.sync()
+    assert np.array_equal(y.cpu().numpy(), oracle.radix_sort(x.cpu().numpy()))
+    m = 20_000_000
+    k = inputs.generate("distinct16", m, torch.int64, seed=1, device="cuda")
+    v = torch.arange(m, dtype=torch.int64, device="cuda").to(torch.int32).view(torch.uint32)
+    ko, vo = torch.empty_like(k), torch.empty_like(v)
+    evo.sort_pairs(k, v, ko, vo, algo="merge", insertion_threshold=32)
+    evo.sync()
+    ek, ev = oracle.radix_sort(k.cpu().numpy(), v.cpu().numpy())
+    assert np.array_equal(ko.cpu().numpy(), ek) and np.array_equal(vo.cpu().numpy(), ev)
 
 
 def test_float64_pairs_5e8_full_oracle(evo):

@@ -415,3 +415,86 @@ def test_adaptive_thresholds_are_parameters(evo):
         evo.profile(False)
     assert {r["pass"]: r["rank"] for r in recs} == {0: 3, 1: 1, 2: 1, 3: 1, 4: 1, 5: 1, 6: 1, 7: 1}
     assert np.array_equal(bits(y), oracle.radix_sort(x.cpu().numpy()).view(np.uint64))
+
+
+def _onesweep_and_fixup(evo, fn):
+    evo.profile(True)
+    try:
+        fn()
+        evo.sync()
+        recs = evo.profile_read()
+    finally:
+        evo.profile(False)
+    active = [r for r in recs if r["kind"] == "radix_onesweep" and r["active"]]
+    fix = [r for r in recs if r["kind"] == "radix_fixup" and r["active"]]
+    return active, fix
+
+
+@pytest.mark.parametrize("dtype", ALL, ids=str)
+def test_presorted_input_is_copied(evo, dtype):
+    """Input already in order (ascending, or descending for a descending
+    sort): no pass runs; out of place it is copied, in place nothing moves;
+    keys and stable pairs match the oracle."""
+    n = 1_234_567
+    x = gen("float_mix" if dtype.is_floating_point else "uniform", n, dtype, seed=3)
+    srt = torch.from_numpy(oracle.radix_sort(x.cpu().numpy())).cuda()
+    y = torch.empty_like(srt)
+    active, fix = _onesweep_and_fixup(evo, lambda: evo.sort(srt, out=y, algo="radix"))
+    assert not active and len(fix) == 1
+    assert torch.equal(y.view(torch.uint8), srt.view(torch.uint8))
+    z = srt.clone()
+    active, fix = _onesweep_and_fixup(evo, lambda: evo.sort(z, algo="radix"))
+    assert not active and not fix and torch.equal(z.view(torch.uint8), srt.view(torch.uint8))
+    run_pairs(evo, srt, algo="radix")
+    # a descending sort of descending keys is the same shortcut
+    sint = torch.int32 if dtype.itemsize == 4 else torch.int64
+    dsc = srt.view(sint).flip(0).contiguous().view(dtype)
+    d = torch.empty_like(dsc)
+    active, _ = _onesweep_and_fixup(evo, lambda: evo.sort(dsc, out=d, algo="radix", descending=True))
+    assert not active and torch.equal(d.view(torch.uint8), dsc.view(torch.uint8))
+
+
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64, torch.float64], ids=str)
+def test_reversed_input_is_reversed(evo, dtype):
+    """Strictly decreasing input: one reversed copy (keys and pairs, in and
+    out of place).  Non-increasing input with equal neighbours: keys take the
+    reversal; pairs take the passes (a reversal would swap equal keys'
+    values)."""
+    n = 2_000_003
+    base = gen("float_mix" if dtype.is_floating_point else "uniform", n, dtype, seed=4)
+    asc = torch.from_numpy(oracle.radix_sort(base.cpu().numpy())).cuda()
+    # strictly decreasing: drop duplicates
+    u = torch.unique_consecutive(asc.view(torch.int32 if dtype.itemsize == 4 else torch.int64))
+    strict = u.flip(0).contiguous().view(dtype)
+    y = torch.empty_like(strict)
+    active, fix = _onesweep_and_fixup(evo, lambda: evo.sort(strict, out=y, algo="radix"))
+    assert not active and len(fix) == 1
+    run_keys(evo, strict, algo="radix")
+    run_keys(evo, strict, inplace=True, algo="radix")
+    run_pairs(evo, strict, algo="radix")
+    run_pairs(evo, strict, inplace=True, algo="radix")
+    # with equal neighbours
+    dup = torch.repeat_interleave(strict[:300_000], 3)
+    active, _ = _onesweep_and_fixup(evo, lambda: evo.sort(dup, out=torch.empty_like(dup), algo="radix"))
+    assert not active
+    run_keys(evo, dup, algo="radix")
+    v = torch.arange(dup.numel(), dtype=torch.int64, device="cuda").to(torch.int32).view(torch.uint32)
+    active, _ = _onesweep_and_fixup(evo, lambda: evo.sort_pairs(dup, v, torch.empty_like(dup), torch.empty_like(v),
+                                                                algo="radix"))
+    assert active, "pairs with equal keys must not take the reversal"
+    run_pairs(evo, dup, algo="radix")
+
+
+def test_one_pair_out_of_order_takes_the_passes(evo):
+    """Sorted input with one swapped neighbour pair (at a chunk boundary and
+    in the middle of a vector): the order check sees it, the passes run."""
+    n = 3_000_000
+    base = torch.arange(n, dtype=torch.int64, device="cuda") * 7 - 5
+    for i in (512 * 16 - 1, 1_500_001, n - 2, 0):
+        x = base.clone()
+        x[i], x[i + 1] = base[i + 1], base[i]
+        active, _ = _onesweep_and_fixup(evo, lambda: evo.sort(x, out=torch.empty_like(x), algo="radix"))
+        assert active, i
+        run_keys(evo, x, algo="radix")
+        x32 = x.to(torch.int32)
+        run_keys(evo, x32, algo="radix")
