@@ -77,8 +77,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1 << 23, help="keys per distribution for the oracle")
     ap.add_argument("--sizes", default="1e7,1e8,1e9,5e9", help="paper9 workload: array sizes")
     ap.add_argument("--workload", default="nine",
-                    choices=["nine", "int32", "floatpairs", "segmented", "u32big", "small", "merge", "paper9",
-                             "friendster"],
+                    choices=["nine", "int32", "floatpairs", "segmented", "u32big", "small", "merge", "serving",
+                             "paper9", "friendster"],
                     help="nine: the headline workload; the others measure the other configurations")
     ap.add_argument("--segments", type=int, default=100_000)
     return ap.parse_args()
@@ -459,7 +459,8 @@ def main():
     extras = {}
     if ws == 1 and not args.no_extras:
         for name, fn in (("int32", leg_int32), ("floatpairs", leg_floatpairs), ("segmented", leg_segmented),
-                         ("u32big", leg_u32big), ("small", leg_small), ("merge", leg_merge)):
+                         ("u32big", leg_u32big), ("small", leg_small), ("merge", leg_merge),
+                         ("serving", leg_serving)):
             try:
                 extras[name] = fn(evo, args, stream, barrier, dev)
             except Exception as exc:   # one configuration's failure does not drop the line
@@ -699,6 +700,7 @@ def leg_small(evo, args, stream, barrier, dev):
             torch.cuda.synchronize()
             dev_us, host_us = [], []
             k0 = evo.kernel_launches()
+            evo.profile(True)
             for _ in range(101):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -709,13 +711,34 @@ def leg_small(evo, args, stream, barrier, dev):
                 torch.cuda.synchronize()
                 host_us.append((time.perf_counter() - t0) * 1e6)
                 dev_us.append(e0.elapsed_time(e1) * 1e3)
-            row[label] = {"device_us_median": statistics.median(dev_us), "host_us_median": statistics.median(host_us),
+            recs = evo.profile_read()
+            evo.profile(False)
+            row[label] = {"call_us_median": statistics.median(dev_us), "host_us_median": statistics.median(host_us),
+                          "kernel_us_per_call": sum(r["ms"] for r in recs) * 1e3 / 101,
                           "launches_per_call": (evo.kernel_launches() - k0) / 101}
         res[str(n)] = row
     return {"unit": "us per sort", "config": {"workload": "one int32 array of 1e3 / 4096 / 1e4 uniform keys per call; "
                                               "'auto' lets the dispatcher choose (one-CTA path up to 4096 keys), "
-                                              "'radix' forces the device-wide radix sort"},
+                                              "'radix' forces the device-wide radix sort; call_us: events around "
+                                              "the Python call on its stream (includes host overhead), "
+                                              "kernel_us: the library's events around its launches"},
             "latency": res}
+
+
+def leg_serving(evo, args, stream, barrier, dev, requests=300):
+    """The serving loop on a Poisson stream of sort requests, sizes
+    log-uniform 1e3..1e8 keys, dtypes int32 / int64 / float64, at 70% of the
+    measured capacity: p50/p99 latency (arrival to completion) and keys/s."""
+    from paper_2505_18681_gb300 import serve
+    evo.table_clear()
+    evo.table_load(os.path.join(TABLE_DIR, "gb300_int32.txt"))   # tuned entries of both key widths
+    res = serve.serve_mix(requests, 100_000_000, table=os.path.join(TABLE_DIR, "gb300_int64.txt"))
+    evo.table_clear()
+    return {"value": res["keys_per_s"] / 1e9, "unit": "GKeys/s", "p50_ms": res["p50_ms"], "p99_ms": res["p99_ms"],
+            "config": {"workload": "%d sort requests, log-uniform sizes 1e3..1e8 keys (largest %d), int32 / int64 / "
+                       "float64, Poisson arrivals at %.0f%% of the measured capacity" % (
+                           requests, res["largest_request"], 100 * res["load"])},
+            "detail": res}
 
 
 def leg_merge(evo, args, stream, barrier, dev):
@@ -787,9 +810,9 @@ def other_workload(args):
         if ws > 1:
             tdist.destroy_process_group()
         return
-    if args.workload in ("floatpairs", "u32big", "small", "merge", "int32"):
+    if args.workload in ("floatpairs", "u32big", "small", "merge", "int32", "serving"):
         leg = {"floatpairs": leg_floatpairs, "u32big": leg_u32big, "small": leg_small, "merge": leg_merge,
-               "int32": leg_int32}[args.workload]
+               "int32": leg_int32, "serving": leg_serving}[args.workload]
         line.update(leg(evo, args, stream, lambda: None, torch.device("cuda")))
         print(json.dumps(line), flush=True)
         return

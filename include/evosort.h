@@ -246,6 +246,14 @@ evosort_status evosort_classify(const void* keys, size_t n, evosort_dtype dt, vo
 evosort_status evosort_plan(const void* keys, size_t n, evosort_dtype dt, void* stream, evosort_params* out,
                             int* cls);
 
+/* The same plan for keys in HOST memory: the strided sample is read directly
+ * on the host (no CUDA call, no synchronisation), so a caller that holds a
+ * host copy (a serving loop, a host batch) can plan a sort before its upload.
+ * descending != 0 reads the class in the order of a descending sort.  The
+ * returned stream and workspace are NULL. */
+evosort_status evosort_plan_host(const void* keys, size_t n, evosort_dtype dt, int descending,
+                                 evosort_params* out, int* cls);
+
 /* Table of tuned parameters: set one entry (ms = its measured time, kept for
  * reference), clear, count, save to / load from a text file (one entry per
  * line: dtype size_bucket class algo digit_bits block_size keys_per_thread

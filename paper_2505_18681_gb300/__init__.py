@@ -120,6 +120,8 @@ def library():
             lib.evosort_classify.restype = st
             lib.evosort_plan.argtypes = [vp, sz, i, vp, pp, ctypes.POINTER(ctypes.c_int)]
             lib.evosort_plan.restype = st
+            lib.evosort_plan_host.argtypes = [vp, sz, i, i, pp, ctypes.POINTER(ctypes.c_int)]
+            lib.evosort_plan_host.restype = st
             lib.evosort_table_set.argtypes = [i, i, i, pp, ctypes.c_float]
             lib.evosort_table_set.restype = st
             lib.evosort_table_clear.argtypes = []
@@ -308,6 +310,11 @@ def set_wait_limit(polls: int) -> None:
     library().evosort_set_wait_limit(int(polls))
 
 
+def segmented_workspace_bytes(total: int, nseg: int, dtype: torch.dtype) -> int:
+    """Scratch bytes of a batched segmented sort of total keys in nseg segments."""
+    return int(library().evosort_segmented_workspace_bytes(total, nseg, DTYPES[dtype]))
+
+
 def kernel_launches() -> int:
     """Kernels launched by the library in this process so far."""
     return int(library().evosort_kernel_launches())
@@ -353,6 +360,20 @@ def plan(keys: torch.Tensor, stream=None):
     c = ctypes.c_int(0)
     _check(library().evosort_plan(keys.data_ptr(), keys.numel(), _dtype_code(keys), _stream_handle(stream),
                                   ctypes.byref(p), ctypes.byref(c)))
+    return params_dict(p), CLASSES[c.value]
+
+
+def plan_host(keys: torch.Tensor, descending: bool = False):
+    """(params dict, class) for keys in host memory, classified from a
+    strided sample read on the host (no device access)."""
+    if keys.is_cuda:
+        raise ValueError("plan_host takes a CPU tensor")
+    if not keys.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    p = Params()
+    c = ctypes.c_int(0)
+    _check(library().evosort_plan_host(keys.data_ptr(), keys.numel(), _dtype_code(keys), int(descending),
+                                       ctypes.byref(p), ctypes.byref(c)))
     return params_dict(p), CLASSES[c.value]
 
 

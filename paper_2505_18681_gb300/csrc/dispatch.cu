@@ -281,4 +281,23 @@ evosort_status evosort_plan(const void* keys, size_t n, evosort_dtype dt, void* 
     return plan_for(keys, n, dt, stream, false, out, cls_out);
 }
 
+evosort_status evosort_plan_host(const void* keys, size_t n, evosort_dtype dt, int descending, evosort_params* out,
+                                 int* cls_out) {
+    set_error("");
+    if (!out || (n && !keys) || dt < EVOSORT_I32 || dt > EVOSORT_F64) {
+        set_error("evosort_plan_host: bad argument");
+        return EVOSORT_ERR_INVALID;
+    }
+    evosort_default_params(out);
+    int cls = EVOSORT_CLASS_RANDOM;
+    if (table_nonempty() && n >= 2) {
+        cls = classify_host(keys, n, dt, descending != 0);
+        table_lookup(dt, n, cls, out);
+        out->stream = nullptr;
+    }
+    out->descending = descending ? 1 : 0;
+    if (cls_out) *cls_out = cls;
+    return EVOSORT_OK;
+}
+
 }  // extern "C"
