@@ -148,6 +148,16 @@ void evosort_default_params(evosort_params* p);
 size_t evosort_workspace_bytes(size_t n, evosort_dtype dt, int with_values,
                                const evosort_params* p);
 
+/* The parameters a sort of n keys of dtype dt (with values if with_values)
+ * would run with under params p (NULL = defaults), every default resolved:
+ * algorithm, pass kernel, tile shape (with n known the default tile follows
+ * the closed form fitted to the tuned tables over log10 n, guarded so that
+ * small inputs still give half of the SMs a tile), ranking, thresholds.  The
+ * dispatcher's table is not consulted (that needs the keys: evosort_plan).
+ * Host only. */
+evosort_status evosort_resolve(size_t n, evosort_dtype dt, int with_values, const evosort_params* p,
+                               evosort_params* out);
+
 /* Sorts keys[0..n) in place (AdaptivePartitionSort, Algorithm 5).
  * keys: device array of n elements of dtype dt. */
 evosort_status evosort_sort(void* keys, size_t n, evosort_dtype dt, const evosort_params* p);

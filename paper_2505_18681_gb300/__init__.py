@@ -103,6 +103,8 @@ def library():
             lib.evosort_default_params.restype = None
             lib.evosort_workspace_bytes.argtypes = [sz, i, i, pp]
             lib.evosort_workspace_bytes.restype = sz
+            lib.evosort_resolve.argtypes = [sz, i, i, pp, pp]
+            lib.evosort_resolve.restype = st
             lib.evosort_sort.argtypes = [vp, sz, i, pp]
             lib.evosort_sort_to.argtypes = [vp, vp, sz, i, pp]
             lib.evosort_sort_pairs.argtypes = [vp, vp, sz, i, pp]
@@ -361,6 +363,15 @@ def plan(keys: torch.Tensor, stream=None):
     _check(library().evosort_plan(keys.data_ptr(), keys.numel(), _dtype_code(keys), _stream_handle(stream),
                                   ctypes.byref(p), ctypes.byref(c)))
     return params_dict(p), CLASSES[c.value]
+
+
+def resolve(n: int, dtype: torch.dtype, with_values: bool = False, **kw) -> dict:
+    """Every parameter a sort of n keys would run with (defaults resolved;
+    no table lookup); keyword arguments as for make_params."""
+    out = Params()
+    p = make_params(**kw)
+    _check(library().evosort_resolve(n, DTYPES[dtype], int(with_values), ctypes.byref(p), ctypes.byref(out)))
+    return params_dict(out)
 
 
 def plan_host(keys: torch.Tensor, descending: bool = False):

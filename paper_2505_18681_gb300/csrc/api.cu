@@ -10,6 +10,7 @@
 
 #include "evosort.h"
 #include "api_internal.h"
+#include "closed_form.h"
 #include "radix_launch.cuh"
 
 namespace evosort {
@@ -330,13 +331,45 @@ static void reg_prefs(int w, bool pairs, const int (**pref)[2], int* np) {
 // tile (n / tile < SMs / 2) and a smaller preferred shape fits: small sorts
 // then fill the GPU.  (The GA's winners at 2^20 keys follow this rule: 8K-key
 // tiles for 32-bit keys, against 16K above 2^22.)
+// Fitted log2 tile size at n (the closed form of the tuned tables, L = log10 n
+// clamped to the tuned range).
+static double fitted_log2_tile(int w, size_t n) {
+    const double* f = w == 4 ? kTileFit32 : kTileFit64;
+    double L = std::log10((double)(n < 2 ? 2 : n));
+    L = L < f[3] ? f[3] : (L > f[4] ? f[4] : L);
+    return f[0] + f[1] * L + f[2] * L * L;
+}
+
 static void default_tile_shape(int w, bool pairs, Plan* pl, size_t n = 0) {
     const bool given = pl->block_size && pl->keys_per_thread;
     const size_t half = (size_t)(sm_count() / 2);
     if (pl->pass_kernel == 2 || (pl->pass_kernel == 0 && reg_by_default(w, pairs))) {
-        const int(*pref)[2];
+        const int(*pref0)[2];
         int np = 0;
-        reg_prefs(w, pairs, &pref, &np);
+        reg_prefs(w, pairs, &pref0, &np);
+        // with n known, the preference order is by distance from the fitted
+        // tile size (nearest first, ties to the larger tile); the "fills half
+        // the SMs" rule below still guards small inputs
+        int pref[4][2];
+        for (int i = 0; i < np; ++i) {
+            pref[i][0] = pref0[i][0];
+            pref[i][1] = pref0[i][1];
+        }
+        if (n > 0 && !given) {
+            const double t = fitted_log2_tile(w, n);
+            for (int i = 1; i < np; ++i)
+                for (int j = i; j > 0; --j) {
+                    const double da = std::fabs(std::log2((double)pref[j][0] * pref[j][1]) - t);
+                    const double db = std::fabs(std::log2((double)pref[j - 1][0] * pref[j - 1][1]) - t);
+                    const bool larger = pref[j][0] * pref[j][1] > pref[j - 1][0] * pref[j - 1][1];
+                    if (da < db - 1e-9 || (std::fabs(da - db) <= 1e-9 && larger)) {
+                        std::swap(pref[j][0], pref[j - 1][0]);
+                        std::swap(pref[j][1], pref[j - 1][1]);
+                    } else {
+                        break;
+                    }
+                }
+        }
         int chosen = -1;
         for (int i = 0; i < np; ++i) {
             const int b = pl->block_size ? pl->block_size : pref[i][0];
@@ -594,6 +627,37 @@ size_t evosort_workspace_bytes(size_t n, evosort_dtype dt, int with_values, cons
     const int w = dtype_bytes(dt);
     if (pl.algo == EVOSORT_ALGO_MERGE) return merge_workspace_bytes(n, w, with_values != 0, pl);
     return radix_workspace_bytes(n, w, with_values != 0, pl);
+}
+
+evosort_status evosort_resolve(size_t n, evosort_dtype dt, int with_values, const evosort_params* p,
+                               evosort_params* out) {
+    std::string err;
+    set_error("");
+    if (!valid_dtype(dt) || !out) return finish(EVOSORT_ERR_INVALID, "evosort_resolve: bad argument");
+    Plan pl;
+    const int rc = resolve(p, dt, with_values != 0, &pl, &err, n);
+    if (rc) return finish(rc, err);
+    evosort_default_params(out);
+    out->algo = pl.algo;
+    out->digit_bits = pl.digit_bits;
+    out->keys_per_thread = pl.keys_per_thread;
+    out->block_size = pl.block_size;
+    out->insertion_threshold = pl.insertion_threshold;
+    out->rank_mode = pl.rank_mode;
+    out->seg_block_cap = pl.seg_block_cap;
+    out->descending = pl.descending ? 1 : 0;
+    out->pass_kernel = pl.pass_kernel;
+    out->adapt_later = pl.adapt_later;
+    out->adapt_first = pl.adapt_first;
+    out->seg_warp_cap = pl.seg_warp_cap;
+    out->small_cap = pl.small_cap;
+    out->seg_giant = pl.seg_giant;
+    if (p) {
+        out->stream = p->stream;
+        out->workspace = p->workspace;
+        out->workspace_bytes = p->workspace_bytes;
+    }
+    return EVOSORT_OK;
 }
 
 evosort_status evosort_sort(void* keys, size_t n, evosort_dtype dt, const evosort_params* p) {
