@@ -21,7 +21,10 @@
 //   - after the ranking, the first 256 threads own one digit each: they
 //     publish the tile's digit counts and walk the look-back, while the next
 //     256 threads scan the counts and turn the warp counters into reorder
-//     offsets, so the look-back's L2 round trips overlap the scan;
+//     offsets; the scanners then release the other warps to reorder through
+//     a named barrier (arrive / sync) and the owners through another, so the
+//     look-back's L2 round trips overlap the scan and most of the reorder
+//     (three CTA barriers per tile);
 //   - the next tile is claimed only after this tile's look-back is done (and
 //     prefetched into L2 by one bulk prefetch): a claimed tile blocks the
 //     look-back of every later tile until its counts are published, so the
@@ -229,7 +232,6 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
                 }
             }
             const unsigned long long glb = boff[b] + excl;
-            s_glb[b] = glb;
             // the digit's keys land in [glb, glb + count): past n only after an
             // inconsistent look-back (a timed-out wait); the tile's stores are
             // then skipped.  (A partial tile's padding keys count under the
@@ -239,6 +241,16 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
                 s_bad = 1;
                 atomicOr(a.status, ST_RANGE);
             }
+            // the owners' own reorder needs the scanners' offsets
+            __syncwarp();   // the look-back diverged per lane: whole warps at the barrier
+            named_barrier(4, 2 * bins);
+            const unsigned long long gb = glb - s_excl[b];
+            s_gbase[b] = gb;
+            s_gbase32[b] = (uint32_t)gb;
+            // claim the next tile now that this one's look-back is done, and
+            // have the TMA engine pull it into L2 while this tile is reordered
+            // and scattered
+            if (tid == 0) claim(cur ^ 1);
         } else if (tid < 2 * bins) {
             // scanners: exclusive scan of the tile's digit counts, then the
             // warp counters become reorder offsets (digit offset in the tile
@@ -269,18 +281,18 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
                 s_wc[v * bins + b] = run;
                 run += c;
             }
+            // offsets ready: release the other warps (3) and the owners (4);
+            // every scanner wrote a column of every warp's counters, so the
+            // scanners wait for each other before their own reorder
+            if (BLOCK > 2 * bins) asm volatile("bar.arrive 3, %0;" ::"n"(BLOCK - bins) : "memory");
+            asm volatile("bar.arrive 4, %0;" ::"n"(2 * bins) : "memory");
+            named_barrier(1, bins);
+        } else {
+            // the remaining warps reorder as soon as the offsets are ready,
+            // while the owners are still walking the look-back
+            asm volatile("bar.sync 3, %0;" ::"n"(BLOCK - bins) : "memory");
         }
-        __syncthreads();   // B3: offsets, tile offsets and global starts ready
 
-        if (tid < bins) {
-            const unsigned long long gb = s_glb[tid] - s_excl[tid];
-            s_gbase[tid] = gb;
-            s_gbase32[tid] = (uint32_t)gb;
-        }
-        // claim the next tile now that this one's look-back is done, and have
-        // the TMA engine pull it into L2 while this tile is reordered and
-        // scattered
-        if (tid == 0) claim(cur ^ 1);
         // ---- reorder the tile by digit into the reorder buffer (stable)
 #pragma unroll
         for (int i = 0; i < KPT; ++i) {
@@ -291,7 +303,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
                 if (PAIRS) s_rv[pos] = val[PAIRS ? i : 0];
             }
         }
-        __syncthreads();   // B4: tile reordered, bases and next tile ready
+        __syncthreads();   // B3: tile reordered, bases and next tile ready
 
         // ---- coalesced stable scatter to the global digit buckets
         const int nv = s_bad ? 0 : valid;
@@ -308,7 +320,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
             }
         }
         // no barrier: the next tile writes the reorder buffer, bases and
-        // tile offsets only after its B1..B3, which every thread reaches
+        // tile offsets only after its B1 and B2, which every thread reaches
         // after finishing this scatter
     }
 }
