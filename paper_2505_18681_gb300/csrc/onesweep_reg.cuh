@@ -18,13 +18,14 @@
 //     in the warp is a 32-bit shared counter that only the column's leader
 //     lane for that digit updates, with one atomic add that also returns the
 //     old count (one access where a read and a write were);
-//   - after the ranking, the first 256 threads own one digit each: they
-//     publish the tile's digit counts and walk the look-back, while the next
-//     256 threads scan the counts and turn the warp counters into reorder
-//     offsets; the scanners then release the other warps to reorder through
-//     a named barrier (arrive / sync) and the owners through another, so the
+//   - after the ranking, threads 256..511 (scanners) sum each digit's count
+//     over the warps and hand it to threads 0..255 (owners, one digit each)
+//     through a named barrier; the owners publish the counts and walk the
+//     look-back while the scanners scan the counts and turn the warp counters
+//     into reorder offsets, then release the other warps to reorder through
+//     another named barrier and the owners through a third, so the
 //     look-back's L2 round trips overlap the scan and most of the reorder
-//     (three CTA barriers per tile);
+//     (two CTA-wide barriers per tile);
 //   - the next tile is claimed only after this tile's look-back is done (and
 //     prefetched into L2 by one bulk prefetch): a claimed tile blocks the
 //     look-back of every later tile until its counts are published, so the
@@ -54,13 +55,12 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
 constexpr int kRegLookback = 8;
 
 // Shared memory of one register-tile CTA: reorder buffer (keys, then values),
-// per-warp digit counters, match masks (rank mode 3), group partial sums, and
-// per-digit tile offsets, global starts and bases.
+// per-warp digit counters, match masks (rank mode 3), and per-digit tile
+// offsets, tile counts and global bases.
 __host__ __device__ constexpr size_t reg_smem_bytes(int block, int kpt, int w, bool pairs, int d, int rank) {
     return (size_t)block * kpt * (w + (pairs ? 4 : 0)) +                                 // reorder buffer
            (size_t)(block / 32) * ((size_t)1 << d) * 4 * (rank == 3 ? 2 : 1) +          // counters (+ masks)
-           (size_t)(block >> d) * ((size_t)1 << d) * 4 +                                 // group partials
-           ((size_t)1 << d) * (4 + 8 + 8 + 4) + 64;                                      // excl, glb, gbase, gbase32
+           ((size_t)1 << d) * (4 + 4 + 8 + 4) + 64;                                      // excl, cnt, gbase, gbase32
 }
 
 // The register tile needs at least two threads per digit (digit owners and
@@ -73,10 +73,8 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
     constexpr int WARPS = BLOCK / 32;
     constexpr int TILE = BLOCK * KPT;
     constexpr int bins = 1 << D;
-    constexpr int G = BLOCK / bins;          // digit groups of the partial sums
-    constexpr int VPG = WARPS / G;           // warps per group
     static_assert(reg_shape_ok(BLOCK, D), "register tile needs BLOCK >= 2 * bins");
-    static_assert(WARPS % G == 0 && RANK != 2, "tile shape / ranking");
+    static_assert(RANK != 2, "ranking");
     const PassDesc desc = a.desc[pass];
     if (!desc.active || (a.adapt && desc.rank != RANK)) return;
 
@@ -90,10 +88,9 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
     uint32_t* s_rv = (uint32_t*)(smem + (size_t)TILE * sizeof(U));
     uint32_t* s_wc = (uint32_t*)(smem + (size_t)TILE * (sizeof(U) + (PAIRS ? 4 : 0)));
     uint32_t* s_wm = s_wc + WARPS * bins;                                  // rank mode 3 only
-    uint32_t* s_part = s_wm + (RANK == 3 ? WARPS * bins : 0);              // G x bins
-    uint32_t* s_excl = s_part + G * bins;                                  // tile offset of each digit
-    unsigned long long* s_glb = (unsigned long long*)(s_excl + bins);      // global start of each digit
-    unsigned long long* s_gbase = s_glb + bins;                            // s_glb - s_excl
+    uint32_t* s_excl = s_wm + (RANK == 3 ? WARPS * bins : 0);              // tile offset of each digit
+    uint32_t* s_cnt = s_excl + bins;                                       // tile count of each digit
+    unsigned long long* s_gbase = (unsigned long long*)(s_cnt + bins);     // global start - tile offset
     uint32_t* s_gbase32 = (uint32_t*)(s_gbase + bins);
     __shared__ uint32_t s_tile[2];
     __shared__ uint32_t s_wtot[WARPS];
@@ -195,24 +192,13 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
         }
         __syncthreads();   // B1: every warp's digit counts are final
 
-        // ---- partial sums of the digit counts over groups of warps
-        if (tid == 0) s_bad = 0;
-        {
-            const int b = tid % bins, g = tid / bins;
-            uint32_t sum = 0;
-#pragma unroll 8
-            for (int v = 0; v < VPG; ++v) sum += s_wc[(g * VPG + v) * bins + b];
-            s_part[g * bins + b] = sum;
-        }
-        __syncthreads();   // B2: partial sums ready
-
         if (tid < bins) {
-            // digit owners: publish the tile's count of digit b, walk the
-            // look-back to the digit's global start for this tile
+            // digit owners: publish the tile's count of digit b (summed over
+            // the warps), walk the look-back to the digit's global start
             const int b = tid;
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int g = 0; g < G; ++g) cnt += s_part[g * bins + b];
+            if (tid == 0) s_bad = 0;   // set again only after barrier 4
+            named_barrier(2, 2 * bins);   // the scanners' digit counts
+            const uint32_t cnt = s_cnt[b];
             const size_t slot0 = (size_t)pass * a.ntiles * bins + b;
             const size_t slot = slot0 + (size_t)tile * bins;
             if (a.lb64)
@@ -237,13 +223,13 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
             // then skipped.  (A partial tile's padding keys count under the
             // digit of an all-ones key but are never stored.)
             const uint32_t pad = (!full && b == (int)digit_of(~(U)0, shift, mask)) ? (uint32_t)(TILE - valid) : 0u;
+            // the owners' own reorder needs the scanners' offsets
+            __syncwarp();   // the look-back diverged per lane: whole warps at the barrier
+            named_barrier(4, 2 * bins);
             if (glb + (cnt - pad) > n) {
                 s_bad = 1;
                 atomicOr(a.status, ST_RANGE);
             }
-            // the owners' own reorder needs the scanners' offsets
-            __syncwarp();   // the look-back diverged per lane: whole warps at the barrier
-            named_barrier(4, 2 * bins);
             const unsigned long long gb = glb - s_excl[b];
             s_gbase[b] = gb;
             s_gbase32[b] = (uint32_t)gb;
@@ -257,8 +243,10 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
             // + count of the digit in earlier warps)
             const int b = tid - bins;
             uint32_t cnt = 0;
-#pragma unroll
-            for (int g = 0; g < G; ++g) cnt += s_part[g * bins + b];
+#pragma unroll 8
+            for (int v = 0; v < WARPS; ++v) cnt += s_wc[v * bins + b];
+            s_cnt[b] = cnt;
+            asm volatile("bar.arrive 2, %0;" ::"n"(2 * bins) : "memory");
             uint32_t inc = cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -320,7 +308,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
             }
         }
         // no barrier: the next tile writes the reorder buffer, bases and
-        // tile offsets only after its B1 and B2, which every thread reaches
+        // tile offsets only after its B1, which every thread reaches
         // after finishing this scatter
     }
 }
