@@ -683,18 +683,53 @@ def leg_u32big(evo, args, stream, barrier, dev):
             "gpu_launches": launches}
 
 
+def small_graph_us(evo, x, y, kw, reps=100):
+    """Device time of one sort with no host in the loop: `reps` sorts captured
+    in one CUDA graph on a side stream, the graph replayed and timed with
+    events (median of 5 replays), divided by reps."""
+    import torch
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    q = evo.make_params(stream=gs, **kw)
+    with torch.cuda.stream(gs):
+        evo.sort(x, out=y, params=q)          # pool warm-up outside the capture
+        gs.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=gs):
+            for _ in range(reps):
+                evo.sort(x, out=y, params=q)
+        g.replay()
+        gs.synchronize()
+        ts = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(gs)
+            g.replay()
+            e1.record(gs)
+            gs.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3 / reps)
+    torch.cuda.current_stream().wait_stream(gs)
+    del g
+    return statistics.median(ts)
+
+
 def leg_small(evo, args, stream, barrier, dev):
     """Latency of small sorts: the dispatcher's one-CTA path (the default for
     arrays up to 4096 keys) against the device-wide radix path, per call."""
     import torch
     from paper_2505_18681_gb300 import inputs
+    # no tuned table: above the one-CTA cut-over 'auto' then takes the default
+    # radix plan with no sample of the keys (a sample reads back to the host,
+    # which a graph capture does not allow)
+    evo.table_clear()
     res = {}
     for n in (1000, 4096, 10_000):
         x = inputs.generate("uniform", n, torch.int32, seed=42, device=dev)
         y = torch.empty_like(x)
         row = {}
-        for label, p in (("auto", evo.make_params(stream=stream)),
-                         ("radix", evo.make_params(algo="radix", stream=stream))):
+        for label, kw in (("auto", {}), ("radix", {"algo": "radix"})):
+            p = evo.make_params(stream=stream, **kw)
             for _ in range(20):
                 evo.sort(x, out=y, params=p)
             torch.cuda.synchronize()
@@ -715,13 +750,16 @@ def leg_small(evo, args, stream, barrier, dev):
             evo.profile(False)
             row[label] = {"call_us_median": statistics.median(dev_us), "host_us_median": statistics.median(host_us),
                           "kernel_us_per_call": sum(r["ms"] for r in recs) * 1e3 / 101,
-                          "launches_per_call": (evo.kernel_launches() - k0) / 101}
+                          "launches_per_call": (evo.kernel_launches() - k0) / 101,
+                          "graph_us_per_sort": small_graph_us(evo, x, y, kw)}
         res[str(n)] = row
     return {"unit": "us per sort", "config": {"workload": "one int32 array of 1e3 / 4096 / 1e4 uniform keys per call; "
                                               "'auto' lets the dispatcher choose (one-CTA path up to 4096 keys), "
                                               "'radix' forces the device-wide radix sort; call_us: events around "
                                               "the Python call on its stream (includes host overhead), "
-                                              "kernel_us: the library's events around its launches"},
+                                              "kernel_us: the library's events around its launches (includes "
+                                              "launch latency), graph_us: device time per sort from a replayed "
+                                              "CUDA graph of 100 sorts"},
             "latency": res}
 
 
