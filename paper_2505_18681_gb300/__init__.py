@@ -21,7 +21,7 @@ import torch
 
 from . import _build
 
-__all__ = ["sort", "sort_pairs", "segmented_sort", "sync", "workspace_bytes", "kernel_launches", "set_wait_limit",
+__all__ = ["sort", "sort_pairs", "segmented_sort", "sync", "release", "workspace_bytes", "kernel_launches", "set_wait_limit",
            "profile", "profile_read",
            "EvoSortError", "Params", "library", "DTYPES"]
 
@@ -152,6 +152,8 @@ def library():
             lib.evosort_profile_read.restype = sz
             lib.evosort_kernel_launches.argtypes = []
             lib.evosort_kernel_launches.restype = ctypes.c_uint64
+            lib.evosort_release.argtypes = []
+            lib.evosort_release.restype = st
             lib.evosort_set_wait_limit.argtypes = [ctypes.c_uint32]
             lib.evosort_set_wait_limit.restype = None
             _lib = lib
@@ -304,6 +306,12 @@ def sync(stream=None) -> None:
 def workspace_bytes(n: int, dtype: torch.dtype, with_values: bool = False, **kw) -> int:
     p = make_params(**kw)
     return int(library().evosort_workspace_bytes(n, DTYPES[dtype], int(with_values), ctypes.byref(p)))
+
+
+def release() -> None:
+    """Waits for the device and returns the library's pooled scratch memory
+    on the current device to the driver (evosort_release)."""
+    _check(library().evosort_release())
 
 
 def set_wait_limit(polls: int) -> None:

@@ -768,6 +768,18 @@ evosort_status evosort_sync(void* stream) {
     return EVOSORT_OK;
 }
 
+evosort_status evosort_release(void) {
+    set_error("");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();   // every stream-ordered free has run
+    cudaMemPool_t pool;
+    if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, dev);
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    if (e != cudaSuccess) return finish(EVOSORT_ERR_CUDA, std::string("release: ") + cudaGetErrorString(e));
+    return EVOSORT_OK;
+}
+
 const char* evosort_last_error(void) { return t_err.c_str(); }
 
 void evosort_set_wait_limit(uint32_t polls) { g_wait_limit.store(polls, std::memory_order_relaxed); }
