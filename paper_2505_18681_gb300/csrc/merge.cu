@@ -8,8 +8,9 @@
 //   K4 merge_block_sort   one CTA per tile of T = T_ins * 2^m keys (the largest
 //                         such tile that fits): loads the tile into shared
 //                         memory, insertion-sorts its base runs (one thread per
-//                         run), then performs the in-tile merge rounds in shared
-//                         memory with merge-path splits per thread;
+//                         run, in registers for runs of up to 32 4-byte or 16
+//                         8-byte keys), then performs the in-tile merge rounds
+//                         in shared memory with merge-path splits per thread;
 //   K5 merge_partition    for each global round, the merge-path split of every
 //                         output tile boundary (binary search along the
 //                         cross-diagonal of the two runs of its pair);
@@ -45,6 +46,12 @@ struct MergeArgs {
     int btile;       // block-sort tile: tins * 2^m <= kMTile
 };
 
+// Shared arrays of a tile are padded with one word per 32: index i lives at
+// i + i / 32, so lanes whose positions lie a power of two apart (a thread's
+// run or its block of outputs) fall in different banks.
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+constexpr int kMTilePad = kMTile + kMTile / 32;
+
 // ---------------------------------------------------------------------------
 // K4: block sort of one tile (base runs insertion-sorted, then merged).
 // ---------------------------------------------------------------------------
@@ -52,27 +59,44 @@ template <typename U, bool PAIRS>
 __global__ void __launch_bounds__(kMB) merge_block_sort(MergeArgs a, int dst_sel, int last) {
     extern __shared__ __align__(16) unsigned char smem[];
     U* k0 = (U*)smem;
-    U* k1 = k0 + kMTile;
-    uint32_t* v0 = (uint32_t*)(k1 + kMTile);
-    uint32_t* v1 = v0 + (PAIRS ? kMTile : 0);
+    U* k1 = k0 + kMTilePad;
+    uint32_t* v0 = (uint32_t*)(k1 + kMTilePad);
+    uint32_t* v1 = v0 + (PAIRS ? kMTilePad : 0);
     const int T = a.btile;
     const size_t base = (size_t)blockIdx.x * T;
     const int len = (int)((a.n - base) < (size_t)T ? (a.n - base) : (size_t)T);
     const U* src = (const U*)a.in;
-    for (int i = threadIdx.x; i < len; i += kMB) {
-        k0[i] = map_fwd(src[base + i], a.map);
-        if (PAIRS) v0[i] = a.vin[base + i];
+    {
+        // every load of a thread is issued before its shared stores
+        U t[kMEPT];
+        uint32_t tv[PAIRS ? kMEPT : 1];
+#pragma unroll
+        for (int r = 0; r < kMEPT; ++r) {
+            const int i = r * kMB + threadIdx.x;
+            if (i < len) {
+                t[r] = src[base + i];
+                if (PAIRS) tv[PAIRS ? r : 0] = a.vin[base + i];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kMEPT; ++r) {
+            const int i = r * kMB + threadIdx.x;
+            if (i < len) {
+                k0[pad32(i)] = map_fwd(t[r], a.map);
+                if (PAIRS) v0[pad32(i)] = tv[PAIRS ? r : 0];
+            }
+        }
     }
     __syncthreads();
     // insertion-sorted base runs, then the in-tile merge rounds (Algorithm 3)
-    const int which = smem_merge_sort<U, PAIRS>(k0, k1, v0, v1, len, a.tins);
+    const int which = smem_merge_sort<U, PAIRS, reg_run_max<U>(), true>(k0, k1, v0, v1, len, a.tins);
     const U* ks = which ? k1 : k0;
     const uint32_t* vs = which ? v1 : v0;
     U* dst = dst_sel ? (U*)a.tmp : (U*)a.out;
     uint32_t* vdst = dst_sel ? a.vtmp : a.vout;
     for (int i = threadIdx.x; i < len; i += kMB) {
-        dst[base + i] = last ? map_inv(ks[i], a.map) : ks[i];
-        if (PAIRS) vdst[base + i] = vs[i];
+        dst[base + i] = last ? map_inv(ks[pad32(i)], a.map) : ks[pad32(i)];
+        if (PAIRS) vdst[base + i] = vs[pad32(i)];
     }
 }
 
@@ -97,6 +121,12 @@ __global__ void __launch_bounds__(256) merge_partition(const U* __restrict__ src
 
 // ---------------------------------------------------------------------------
 // K6: one output tile of a global merge round.
+// The tile's slices of the two runs are staged in shared memory, each thread
+// merges kMEPT consecutive outputs from its merge-path split, and the tile is
+// written back coalesced.  The staging arrays are padded with one word per 32
+// (index i lives at i + i / 32), so the lanes of a warp, whose outputs and
+// split points lie about kMEPT keys apart, fall in different banks; the merge
+// keeps the head key of each run in a register, one shared load per output.
 // ---------------------------------------------------------------------------
 template <typename U, bool PAIRS>
 __global__ void __launch_bounds__(kMB) merge_pass(const U* __restrict__ src, U* __restrict__ dst,
@@ -104,10 +134,10 @@ __global__ void __launch_bounds__(kMB) merge_pass(const U* __restrict__ src, U* 
                                                   size_t n, size_t w, const size_t* __restrict__ split, KeyMap map,
                                                   int last) {
     extern __shared__ __align__(16) unsigned char smem[];
-    U* sk = (U*)smem;                          // staged slices
-    U* so = sk + kMTile;                       // merged output
-    uint32_t* sv = (uint32_t*)(so + kMTile);
-    uint32_t* sov = sv + (PAIRS ? kMTile : 0);
+    U* sk = (U*)smem;                          // staged slices (padded)
+    U* so = sk + kMTilePad;                    // merged output (padded)
+    uint32_t* sv = (uint32_t*)(so + kMTilePad);
+    uint32_t* sov = sv + (PAIRS ? kMTilePad : 0);
     const size_t j = blockIdx.x;
     const size_t o0 = j * kMTile;
     const size_t o1 = o0 + kMTile < n ? o0 + kMTile : n;
@@ -131,39 +161,60 @@ __global__ void __launch_bounds__(kMB) merge_pass(const U* __restrict__ src, U* 
         const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
         const U* A = src + pbase + a0;
         const U* B = src + pbase + la + b0;
-        for (int i = threadIdx.x; i < na + nb; i += kMB) {
-            const bool inA = i < na;
-            sk[i] = inA ? A[i] : B[i - na];
-            if (PAIRS) sv[i] = inA ? vsrc[pbase + a0 + i] : vsrc[pbase + la + b0 + (i - na)];
+        const int cnt = na + nb;
+        {
+            // all of a thread's loads are issued before its shared stores, so
+            // kMEPT of them are in flight at once
+            U t[kMEPT];
+            uint32_t tv[PAIRS ? kMEPT : 1];
+#pragma unroll
+            for (int r = 0; r < kMEPT; ++r) {
+                const int i = r * kMB + threadIdx.x;
+                if (i < cnt) {
+                    const bool inA = i < na;
+                    t[r] = inA ? A[i] : B[i - na];
+                    if (PAIRS) tv[PAIRS ? r : 0] = inA ? vsrc[pbase + a0 + i] : vsrc[pbase + la + b0 + (i - na)];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kMEPT; ++r) {
+                const int i = r * kMB + threadIdx.x;
+                if (i < cnt) {
+                    sk[pad32(i)] = t[r];
+                    if (PAIRS) sv[pad32(i)] = tv[PAIRS ? r : 0];
+                }
+            }
         }
         __syncthreads();
-        const int cnt = na + nb;
-        const int chunk = (cnt + kMB - 1) / kMB;
-        const int q0 = threadIdx.x * chunk < cnt ? threadIdx.x * chunk : cnt;
-        const int q1 = q0 + chunk < cnt ? q0 + chunk : cnt;
+        const int q0 = threadIdx.x * kMEPT < cnt ? threadIdx.x * kMEPT : cnt;
+        const int q1 = q0 + kMEPT < cnt ? q0 + kMEPT : cnt;
         if (q0 < q1) {
-            const U* SA = sk;
-            const U* SB = sk + na;
-            int ia = (int)merge_path<U>([&](size_t i) { return SA[i]; }, na, [&](size_t i) { return SB[i]; }, nb,
-                                        (size_t)q0);
+            int ia = (int)merge_path<U>([&](size_t i) { return sk[pad32((int)i)]; }, na,
+                                        [&](size_t i) { return sk[pad32(na + (int)i)]; }, nb, (size_t)q0);
             int ib = q0 - ia;
+            U ha = ia < na ? sk[pad32(ia)] : (U)0;
+            U hb = ib < nb ? sk[pad32(na + ib)] : (U)0;
+#pragma unroll 4
             for (int q = q0; q < q1; ++q) {
-                const bool takeB = ia >= na || (ib < nb && SB[ib] < SA[ia]);
+                // the right run's key goes first only when strictly smaller: stable
+                const bool takeB = ia >= na || (ib < nb && hb < ha);
                 if (takeB) {
-                    so[q] = SB[ib];
-                    if (PAIRS) sov[q] = sv[na + ib];
+                    so[pad32(q)] = hb;
+                    if (PAIRS) sov[pad32(q)] = sv[pad32(na + ib)];
                     ++ib;
+                    if (ib < nb) hb = sk[pad32(na + ib)];
                 } else {
-                    so[q] = SA[ia];
-                    if (PAIRS) sov[q] = sv[ia];
+                    so[pad32(q)] = ha;
+                    if (PAIRS) sov[pad32(q)] = sv[pad32(ia)];
                     ++ia;
+                    if (ia < na) ha = sk[pad32(ia)];
                 }
             }
         }
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += kMB) {
-            dst[o + i] = last ? map_inv(so[i], map) : so[i];
-            if (PAIRS) vdst[o + i] = sov[i];
+            dst[o + i] = last ? map_inv(so[pad32(i)], map) : so[pad32(i)];
+            if (PAIRS) vdst[o + i] = sov[pad32(i)];
         }
         __syncthreads();
         o = e;
@@ -180,7 +231,7 @@ int merge_sort_t(const MergeArgs& a0, void* ws, cudaStream_t s, std::string* err
     for (size_t w = (size_t)a.btile; w < n; w <<= 1) ++rounds;
     const size_t ntiles = (n + kMTile - 1) / kMTile;
     size_t* split = (size_t*)ws;
-    const size_t smem_block = (size_t)2 * kMTile * (sizeof(U) + (PAIRS ? 4 : 0));
+    const size_t smem_block = (size_t)2 * kMTilePad * (sizeof(U) + (PAIRS ? 4 : 0));
     const size_t smem_pass = smem_block;
     static bool configured = false;
     if (!configured) {

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_sort_kernel(const U* in, 
         if (PAIRS) v0[i] = vin[i];
     }
     __syncthreads();
-    const int which = smem_merge_sort<U, PAIRS>(k0, k1, v0, v1, n, tins);
+    const int which = smem_merge_sort<U, PAIRS, kSmallRun>(k0, k1, v0, v1, n, tins);
     const U* ks = which ? k1 : k0;
     const uint32_t* vs = which ? v1 : v0;
     // in place (in == out) is safe: every input was read before the sort
