@@ -128,8 +128,15 @@ __global__ void __launch_bounds__(256) merge_partition(const U* __restrict__ src
 // split points lie about kMEPT keys apart, fall in different banks; the merge
 // keeps the head key of each run in a register, one shared load per output.
 // ---------------------------------------------------------------------------
+// resident CTAs per SM the register budget allows for: 6 for 4-byte keys
+// alone, 4 with values or for 8-byte keys, 2 for 8-byte keys with values
 template <typename U, bool PAIRS>
-__global__ void __launch_bounds__(kMB) merge_pass(const U* __restrict__ src, U* __restrict__ dst,
+__host__ __device__ constexpr int merge_pass_ctas() {
+    return sizeof(U) == 4 ? (PAIRS ? 4 : 6) : (PAIRS ? 2 : 4);
+}
+
+template <typename U, bool PAIRS>
+__global__ void __launch_bounds__(kMB, merge_pass_ctas<U, PAIRS>()) merge_pass(const U* __restrict__ src, U* __restrict__ dst,
                                                   const uint32_t* __restrict__ vsrc, uint32_t* __restrict__ vdst,
                                                   size_t n, size_t w, const size_t* __restrict__ split, KeyMap map,
                                                   int last) {
