@@ -86,7 +86,7 @@ typedef struct {
                                  half of the SMs a tile */
     int insertion_threshold;  /* mergesort base-run length T_insertion, 2..2048
                                  (default 32; Section 4.2 bounds); the one-CTA
-                                 small-array path caps its runs at 4 keys */
+                                 small-array path caps its runs at 16 keys */
     int rank_mode;            /* radix tile ranking (how a warp finds lanes with
                                  equal digits): 1 = match.any (d = 8 only),
                                  2 = one ballot per digit bit (any d),
