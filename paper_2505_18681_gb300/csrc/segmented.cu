@@ -162,6 +162,9 @@ __device__ void large_tier(const SegArgs& a, unsigned char* smem, uint64_t lo, u
     for (int i = tid; i < NP * BINS; i += kSB) s_hist[i] = 0;
     if (tid < NP) s_active[tid] = 0;
     __syncthreads();
+    // one read of the segment for every pass's digit counts (unrolled, so
+    // several of a thread's loads are in flight)
+#pragma unroll 4
     for (uint64_t i = tid; i < len; i += kSB) {
         const U k = map_fwd(keys[i], a.map);
 #pragma unroll
@@ -204,14 +207,18 @@ __device__ void large_tier(const SegArgs& a, unsigned char* smem, uint64_t lo, u
             U key[kLKPT];
             uint32_t dr[kLKPT];
             const int wofs = warp * 32 * kLKPT + lane;
+            // the tile's keys are all loaded before the ranking starts, so a
+            // warp waits for one round trip per tile, not one per column
 #pragma unroll
             for (int i = 0; i < kLKPT; ++i) {
                 const int s = wofs + 32 * i;
-                U k = ~(U)0;
-                if (s < valid) {
-                    k = src[t0 + s];
-                    if (first) k = map_fwd(k, a.map);
-                }
+                key[i] = s < valid ? src[t0 + s] : ~(U)0;
+            }
+#pragma unroll
+            for (int i = 0; i < kLKPT; ++i) {
+                const int s = wofs + 32 * i;
+                U k = key[i];
+                if (first && s < valid) k = map_fwd(k, a.map);
                 key[i] = k;
                 const uint32_t dig = digit_of(k, shift, 0xFFu);
                 atomicOr(&wm[dig], 1u << lane);
