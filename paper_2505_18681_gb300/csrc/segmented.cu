@@ -59,6 +59,14 @@ struct SegArgs {
 
 __device__ __forceinline__ int len_bucket(uint64_t len) { return 63 - __clzll((long long)len); }
 
+// L2 prefetch of the 16-byte-aligned part of [p, p + bytes) by the TMA
+// engine (no shared memory is written; nothing outside the range is read).
+__device__ __forceinline__ void prefetch_l2_inner(const void* p, size_t bytes) {
+    const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
 // A segment is sorted only if it lies inside the array: lo <= hi <= total.
 // Any other segment is reported (ST_BAD_OFFSETS) and left out of the work
 // list, so no tier ever reads or writes outside [0, total).  total < 2^40 is
@@ -208,7 +216,12 @@ __device__ void large_tier(const SegArgs& a, unsigned char* smem, uint64_t lo, u
             uint32_t dr[kLKPT];
             const int wofs = warp * 32 * kLKPT + lane;
             // the tile's keys are all loaded before the ranking starts, so a
-            // warp waits for one round trip per tile, not one per column
+            // warp waits for one round trip per tile, not one per column; the
+            // next tile is pulled into L2 meanwhile
+            if (tid == 0 && t0 + kLTile < len) {
+                const uint64_t nv = (len - t0 - kLTile) < (uint64_t)kLTile ? (len - t0 - kLTile) : (uint64_t)kLTile;
+                prefetch_l2_inner(src + t0 + kLTile, nv * sizeof(U));
+            }
 #pragma unroll
             for (int i = 0; i < kLKPT; ++i) {
                 const int s = wofs + 32 * i;
