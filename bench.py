@@ -591,6 +591,35 @@ def leg_floatpairs(evo, args, stream, barrier, dev):
             "gpu_launches": launches}
 
 
+def segmented_block_cap(path, w, total):
+    """seg_block_cap of the tuned segmented entry (class 8) nearest to the
+    batch's size bucket in a table file (the library default if none)."""
+    dt_code = 0 if w == 4 else 1
+    best = None
+    with open(path) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            v = line.split()
+            if int(v[0]) == dt_code and int(v[2]) == 8:
+                d = abs(int(v[1]) - (max(total, 1).bit_length() - 1))
+                if best is None or d < best[0]:
+                    best = (d, int(v[9]))
+    return best[1] if best and best[1] > 0 else (8192 if w == 4 else 4096)
+
+
+def segmented_alg_bytes(lens, w, block_cap):
+    """Algorithmic bytes of one batched segmented sort: 2w per key for a
+    segment one CTA sorts on chip, and the radix formula w + P * 2w per key
+    (P = 8w / 8 passes of 8-bit digits, all active for full-range keys) for
+    the longer ones."""
+    import torch
+    lens = torch.as_tensor(lens, dtype=torch.int64)
+    small = int(lens[lens <= block_cap].sum())
+    big = int(lens[lens > block_cap].sum())
+    return 2 * w * small + (w + w * 2 * w) * big
+
+
 def leg_segmented(evo, args, stream, barrier, dev, nseg=100_000, rank=0, world=1):
     """100,000 int32 arrays with log-uniform lengths 16..1e6 (half uniform,
     half nearly sorted): one batched call with the GA-tuned cut-overs against
@@ -667,6 +696,13 @@ def leg_segmented(evo, args, stream, barrier, dev, nseg=100_000, rank=0, world=1
                 evo.sort(work[a:b], params=plain_p)
     plain_ms = _time_steps(per_array, 1, 1, stream) - copy_ms
     evo.sync()
+    cap = segmented_block_cap(os.path.join(TABLE_DIR, "gb300_int32.txt"), 4, total)
+    alg = segmented_alg_bytes(lens, 4, cap)
+    peak, peak_src = measured_peaks()
+    ach = alg / 1e9 / (ms_t * 1e-3)
+    seg_roof = {"bound": "hbm", "kernel": "seg_sort (whole batch, one persistent launch)", "achieved": ach,
+                "peak": peak, "unit": "GB/s", "frac": ach / peak if peak else None, "traffic": None,
+                "peak_source": peak_src, "algorithmic_bytes_per_batch": alg, "block_cap": cap}
     return {"value": total / (ms_t * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": ms_t, "dtype": "i32",
             "config": {"workload": "batched segmented sort: %d int32 arrays, log-uniform lengths 16..1e6, %d keys "
                        "total, even arrays uniform, odd nearly sorted" % (nseg, total),
@@ -675,6 +711,7 @@ def leg_segmented(evo, args, stream, barrier, dev, nseg=100_000, rank=0, world=1
                          "tuned_over_defaults": ms_d / ms_t},
             "graph": {"value": total / (ms_g * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": ms_g,
                       "path": "the tuned batch captured once into a CUDA graph, replayed each step"},
+            "roofline": seg_roof,
             "plain": {"value": total / (plain_ms * 1e-3) / 1e9, "unit": "GKeys/s", "ms_per_step": plain_ms,
                       "batched_over_plain": plain_ms / ms_t, "calls": len(bounds) - 1,
                       "params": "one sort call per array, library defaults"},
