@@ -97,6 +97,7 @@ struct ProfRecord {
 struct ProfCall {
     PassDesc* host_desc;   // pinned copy, npass + 1 entries (radix calls)
     int ndesc;
+    cudaEvent_t copied;    // recorded after the copy into host_desc
 };
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
@@ -113,7 +114,7 @@ bool prof_enabled() { return g_prof_on; }
 int prof_call_begin(const PassDesc* dev_desc, int ndesc, cudaStream_t) {
     if (!g_prof_on) return -1;
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    ProfCall c{nullptr, 0};
+    ProfCall c{nullptr, 0, nullptr};
     if (dev_desc && ndesc > 0 && g_arena && g_arena_used + ndesc <= kArenaDescs) {
         c.host_desc = g_arena + g_arena_used;
         c.ndesc = ndesc;
@@ -127,8 +128,15 @@ void prof_call_end(int call, cudaStream_t s, const PassDesc* dev_desc) {
     if (call < 0) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfCall& c = g_prof_calls[call];
-    if (c.host_desc && dev_desc)
+    if (c.host_desc && dev_desc) {
         cudaMemcpyAsync(c.host_desc, dev_desc, sizeof(PassDesc) * c.ndesc, cudaMemcpyDeviceToHost, s);
+        // the copy comes after the call's last launch event: the reader waits
+        // for this event, not only for the launches, before it uses the copy
+        if (cudaEventCreateWithFlags(&c.copied, cudaEventDisableTiming) == cudaSuccess)
+            cudaEventRecord(c.copied, s);
+        else
+            c.copied = nullptr;
+    }
 }
 
 ProfScope::ProfScope(int call, int kind, int pass, double bytes, uint64_t items, cudaStream_t s, int rank)
@@ -157,7 +165,7 @@ struct RadixLayout {
     int npass;
     size_t ntiles;
     int lb64;
-    size_t off_desc, off_tiles, off_counts, off_lookback, zero_end, off_tmp, off_vtmp, total;
+    size_t off_desc, off_tiles, off_counts, off_range, off_counts2, off_lookback, zero_end, off_tmp, off_vtmp, total;
 };
 
 static RadixLayout radix_layout(size_t n, int w, bool pairs, const Plan& pl) {
@@ -174,6 +182,10 @@ static RadixLayout radix_layout(size_t n, int w, bool pairs, const Plan& pl) {
     off = align_up(off + (L.npass + 4) * sizeof(uint32_t), 256);   // tile counters, then the order flags
     L.off_counts = off;
     off = align_up(off + L.npass * bins * sizeof(unsigned long long), 256);
+    L.off_range = off;   // RNG_WORDS range words (smallest / largest key, bias, flags)
+    off = align_up(off + RNG_WORDS * sizeof(unsigned long long), 256);
+    L.off_counts2 = off;   // digit counts of the rebased keys (8-bit digits only)
+    off = align_up(off + (pl.digit_bits == 8 ? L.npass * bins * sizeof(unsigned long long) : 0), 256);
     L.off_lookback = off;
     off = align_up(off + (size_t)L.npass * L.ntiles * bins * (L.lb64 ? 8 : 4), 256);
     L.zero_end = off;
@@ -228,6 +240,8 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     a.lookback = base + L.off_lookback;
     a.tile_counter = (uint32_t*)(base + L.off_tiles);
     a.order = a.tile_counter + L.npass;
+    a.range = (unsigned long long*)(base + L.off_range);
+    a.counts2 = (unsigned long long*)(base + L.off_counts2);
     a.status = status;
     const int inplace = (in == out) ? 1 : 0;
 
@@ -243,6 +257,13 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
     {
         ProfScope ps(call, EVOSORT_K_RADIX_HISTOGRAM, -1, (double)n * w, n, s);
         if (e == cudaSuccess) e = launch_radix_aux(w, 0, hist_grid, hist_smem, s, a, inplace);
+    }
+    if (pl.digit_bits == 8) {
+        // K1b: recount the digits of key - min when that leaves fewer passes
+        // (it returns at once otherwise; whether it ran is decided on the
+        // device, so its record carries no bytes)
+        ProfScope ps(call, EVOSORT_K_RADIX_HISTOGRAM, -2, 0.0, n, s);
+        if (e == cudaSuccess) e = launch_radix_aux(w, 3, hist_grid, hist_smem, s, a, inplace);
     }
     {
         ProfScope ps(call, EVOSORT_K_RADIX_SCAN, -1, 0.0, 0, s);
@@ -270,7 +291,7 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
         if (e == cudaSuccess) e = launch_radix_aux(w, 2, fix_grid, 0, s, a, inplace);
     }
     prof_call_end(call, s, a.desc);
-    count_launches(3 + (adapt ? 2 : 1) * L.npass);
+    count_launches(3 + (pl.digit_bits == 8 ? 1 : 0) + (adapt ? 2 : 1) * L.npass);
     if (e != cudaSuccess) {
         *err = std::string("radix launch: ") + cudaGetErrorString(e);
         return EVOSORT_ERR_CUDA;
@@ -808,6 +829,7 @@ size_t evosort_profile_read(evosort_kernel_record* out, size_t cap) {
         cudaEventElapsedTime(&ms, r.e0, r.e1);
         int active = 1;
         const ProfCall& c = g_prof_calls[r.call];
+        if (c.copied) cudaEventSynchronize(c.copied);
         if (c.host_desc) {
             if (r.kind == EVOSORT_K_RADIX_ONESWEEP && r.pass >= 0 && r.pass < c.ndesc)
                 active = c.host_desc[r.pass].active && (r.rank == 0 || c.host_desc[r.pass].rank == r.rank);
@@ -827,6 +849,8 @@ size_t evosort_profile_read(evosort_kernel_record* out, size_t cap) {
         cudaEventDestroy(r.e0);
         cudaEventDestroy(r.e1);
     }
+    for (ProfCall& c : g_prof_calls)
+        if (c.copied) cudaEventDestroy(c.copied);
     g_arena_used = 0;
     g_prof.clear();
     g_prof_calls.clear();

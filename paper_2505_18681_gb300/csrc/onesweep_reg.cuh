@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
     constexpr uint32_t mask = (uint32_t)(bins - 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const KeyMap map = a.map;
+    const U bias = pass_bias<U>(a);   // smallest mapped key when rebased, else 0
 
     extern __shared__ __align__(16) unsigned char smem[];
     U* s_r = (U*)smem;
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
         if (desc.xin) {
 #pragma unroll
             for (int i = 0; i < KPT; ++i)
-                if (full || wofs + 32 * i < valid) key[i] = map_fwd(key[i], map);
+                if (full || wofs + 32 * i < valid) key[i] = rank_key(key[i], map, bias);
         }
 #pragma unroll
         for (int i = 0; i < (KPT + 1) / 2; ++i) rk[i] = 0u;
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(BLOCK, (BLOCK >= 1024 ? 1 : 1024 / BLOCK))
                 const uint32_t dig = digit_of(k, shift, mask);
                 const size_t g = small_n ? (size_t)(uint32_t)(s_gbase32[dig] + (uint32_t)s)
                                          : (size_t)(s_gbase[dig] + (unsigned long long)s);
-                st_stream(dst + g, desc.xout ? map_inv(k, map) : k);
+                st_stream(dst + g, desc.xout ? unrank_key(k, map, bias) : k);
                 if (PAIRS) st_stream(vdst + g, s_rv[s]);
             }
         }

@@ -32,6 +32,11 @@ enum : int { FIX_NONE = 0, FIX_IN_TO_OUT = 1, FIX_TMP_TO_OUT = 2, FIX_REVERSE = 
 // of neighbours that descends, that ascends, that is equal (in the order the
 // sort produces, i.e. on the mapped keys).
 enum : int { ORD_DESCENT = 0, ORD_ASCENT = 1, ORD_EQUAL = 2 };
+// Range words (64-bit, zeroed with the scratch): the largest complement of a
+// mapped key (so ~word = the smallest key), the largest mapped key, the bias
+// the passes subtract (0 unless rebased), and flags.
+enum : int { RNG_NOTMIN = 0, RNG_MAX = 1, RNG_BIAS = 2, RNG_FLAGS = 3, RNG_WORDS = 4 };
+enum : unsigned { RNG_RECORDED = 1u, RNG_REBASED = 2u };
 
 struct PassDesc {
     int active;   // 0: the digit is constant over all keys, pass skipped
@@ -65,8 +70,30 @@ struct RadixArgs {
     void* lookback;             // slots [pass][tile][digit]
     uint32_t* tile_counter;     // npass counters
     uint32_t* order;            // 3 order flags (ORD_*), zeroed with the counters
+    unsigned long long* range;  // RNG_WORDS words (RNG_*), zeroed with the counters
+    unsigned long long* counts2;   // npass << d digit counts of the rebased keys
     uint32_t* status;
 };
+
+// Range reduction ("rebase"): when the mapped keys span fewer 8-bit digits
+// than the raw digits that vary (keys of both signs near zero differ in all
+// their high bytes), the passes rank key - min instead of the key: the same
+// order, with only ceil(bits(max - min) / 8) digits left to sort.  The
+// smallest mapped key is subtracted on the first pass's load and added back
+// on the last pass's store.
+template <typename U>
+__device__ __forceinline__ U rank_key(U raw, const KeyMap& m, U bias) {
+    return map_fwd(raw, m) - bias;
+}
+template <typename U>
+__device__ __forceinline__ U unrank_key(U k, const KeyMap& m, U bias) {
+    return map_inv((U)(k + bias), m);
+}
+// The bias the pass kernels subtract (0 when the sort is not rebased).
+template <typename U>
+__device__ __forceinline__ U pass_bias(const RadixArgs& a) {
+    return a.range ? (U)a.range[RNG_BIAS] : (U)0;
+}
 
 template <typename U>
 __device__ __forceinline__ const U* sel_src(const RadixArgs& a, int s) {
@@ -232,13 +259,47 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram(RadixArgs a) {
 // each pass's counters directly (no run merging: the columns already keep a
 // warp's atomics apart, and merging costs a compare per digit on random
 // keys).  Counters of 64-bit keys use 16 columns (2 lanes per column) to fit
-// 128 KB.  The order relations are recorded as in the generic kernel.
-template <typename U>
+// 128 KB.  The order relations are recorded as in the generic kernel, and so
+// are the smallest and largest mapped keys (RNG_* words).
+// With REBASE (K1b, launched after K1) the kernel first decides whether the
+// sort is rebased: only when the span of the mapped keys needs fewer 8-bit
+// digits than the passes whose raw digit varies.  If not, it returns at
+// once; if so, it counts the digits of key - min into counts2 (and its first
+// CTA publishes the bias), which K2 then uses in place of the raw counts.
+template <typename U, bool REBASE>
 __global__ void __launch_bounds__(kHistThreads) radix_histogram8(RadixArgs a) {
     extern __shared__ uint32_t s_h[];
     constexpr int NP = (int)sizeof(U);
     constexpr int BINS = 256;
     constexpr int COLS = hist_cols(NP, 8);
+    __shared__ unsigned s_triv;
+    __shared__ int s_go;
+    __shared__ U s_bias;
+    if (REBASE) {
+        if (!(a.range[RNG_FLAGS] & RNG_RECORDED)) return;
+        if (threadIdx.x == 0) s_triv = 0u;
+        __syncthreads();
+        // passes whose raw digit is constant (one digit holds every key)
+        for (int i = threadIdx.x; i < NP * BINS; i += blockDim.x)
+            if (a.counts[i] == (unsigned long long)a.n) atomicOr(&s_triv, 1u << (i / BINS));
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int varying = NP - __popc(s_triv);
+            const U mn = (U)~(U)a.range[RNG_NOTMIN];
+            const U span = (U)((U)a.range[RNG_MAX] - mn);
+            const int bits = span ? 64 - __clzll((long long)(unsigned long long)span) : 0;
+            s_go = (bits + 7) / 8 < varying ? 1 : 0;
+            s_bias = mn;
+            if (s_go && blockIdx.x == 0) {
+                a.range[RNG_BIAS] = (unsigned long long)mn;
+                atomicOr(&a.range[RNG_FLAGS], (unsigned long long)RNG_REBASED);
+            }
+        }
+        __syncthreads();
+        if (!s_go) return;
+    }
+    const U bias = REBASE ? s_bias : (U)0;
+    unsigned long long* const cnt_out = REBASE ? a.counts2 : a.counts;
     for (int i = threadIdx.x; i < NP * BINS * COLS; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
 
@@ -263,13 +324,21 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram8(RadixArgs a) {
     };
     bool dsc = false, asc = false, eq = false;
     auto relate = [&](U x, U y) {
+        if (REBASE) return;
         dsc |= x > y;
         asc |= x < y;
         eq |= x == y;
     };
+    U notmin = 0, maxk = 0;   // largest ~key and largest key seen (0 = identity)
+    auto extent = [&](U k) {
+        if (REBASE) return;
+        notmin = (U)~k > notmin ? (U)~k : notmin;
+        maxk = k > maxk ? k : maxk;
+    };
     auto count_key = [&](size_t i) {
         const U k = map_fwd(keys[i], map);
-        add(k);
+        extent(k);
+        add((U)(k - bias));
         if (i + 1 < n) relate(k, map_fwd(keys[i + 1], map));
     };
     if (gtid < head) count_key(gtid);
@@ -287,6 +356,7 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram8(RadixArgs a) {
         }
 #pragma unroll
         for (int j = 0; j < HC; ++j) k[j] = map_fwd(k[j], map);
+        if (!REBASE) {
 #pragma unroll
         for (int j = 0; j < HC / V; ++j) {
 #pragma unroll
@@ -302,17 +372,35 @@ __global__ void __launch_bounds__(kHistThreads) radix_histogram8(RadixArgs a) {
                 if (after < n) relate(k[j * V + V - 1], map_fwd(keys[after], map));
             }
         }
+        }
 #pragma unroll
-        for (int j = 0; j < HC; ++j) add(k[j]);
+        for (int j = 0; j < HC; ++j) {
+            extent(k[j]);
+            add((U)(k[j] - bias));
+        }
     }
-    if (__any_sync(0xffffffffu, dsc) && lane == 0) atomicOr(&a.order[ORD_DESCENT], 1u);
-    if (__any_sync(0xffffffffu, asc) && lane == 0) atomicOr(&a.order[ORD_ASCENT], 1u);
-    if (__any_sync(0xffffffffu, eq) && lane == 0) atomicOr(&a.order[ORD_EQUAL], 1u);
+    if (!REBASE) {
+        if (__any_sync(0xffffffffu, dsc) && lane == 0) atomicOr(&a.order[ORD_DESCENT], 1u);
+        if (__any_sync(0xffffffffu, asc) && lane == 0) atomicOr(&a.order[ORD_ASCENT], 1u);
+        if (__any_sync(0xffffffffu, eq) && lane == 0) atomicOr(&a.order[ORD_EQUAL], 1u);
+        unsigned long long nm = notmin, mx = maxk;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y0 = __shfl_xor_sync(0xffffffffu, nm, o);
+            const unsigned long long y1 = __shfl_xor_sync(0xffffffffu, mx, o);
+            nm = y0 > nm ? y0 : nm;
+            mx = y1 > mx ? y1 : mx;
+        }
+        if (lane == 0) {
+            atomicMax(&a.range[RNG_NOTMIN], nm);
+            atomicMax(&a.range[RNG_MAX], mx);
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.range[RNG_FLAGS], (unsigned long long)RNG_RECORDED);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < NP * BINS; i += blockDim.x) {
         uint32_t sum = 0;
         for (int c = 0; c < COLS; ++c) sum += s_h[i * COLS + ((c + i) & (COLS - 1))];
-        if (sum) atomicAdd(&a.counts[i], (unsigned long long)sum);
+        if (sum) atomicAdd(&cnt_out[i], (unsigned long long)sum);
     }
 }
 
@@ -336,6 +424,11 @@ static __global__ void __launch_bounds__(1024) radix_scan_plan(RadixArgs a, int 
     __shared__ double s_sq[32];
     const int bins = 1 << a.d;
     const int per = (bins + 1023) / 1024;   // consecutive bins per thread (<= 2)
+    // a rebased sort (K1b ran) plans from the digit counts of key - min
+    if (a.range && (a.range[RNG_FLAGS] & RNG_REBASED)) {
+        for (int i = threadIdx.x; i < (a.npass << a.d); i += blockDim.x) a.counts[i] = a.counts2[i];
+        __syncthreads();
+    }
     for (int p = 0; p < a.npass; ++p) {
         unsigned long long* c = a.counts + (size_t)p * bins;
         unsigned long long local[2] = {0, 0};
@@ -537,6 +630,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
     constexpr uint32_t mask = (uint32_t)(bins - 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const KeyMap map = a.map;
+    const U bias = pass_bias<U>(a);   // smallest mapped key when rebased, else 0
 
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* bufs = smem;   // two input tile buffers of KB + VB bytes
@@ -614,7 +708,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
 #pragma unroll
             for (int i = 0; i < KPT; ++i) {
                 U k = s_keys[wofs + 32 * i];
-                if (desc.xin) k = map_fwd(k, map);
+                if (desc.xin) k = rank_key(k, map, bias);
                 dr[i] = digit_of(k, shift, mask);
             }
         } else {
@@ -626,7 +720,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                     const U raw = ld_stream(src + idx);
                     s_keys[wofs + 32 * i] = raw;
                     if (PAIRS) s_vals[wofs + 32 * i] = ld_stream(vsrc + idx);
-                    k = desc.xin ? map_fwd(raw, map) : raw;
+                    k = desc.xin ? rank_key(raw, map, bias) : raw;
                 }
                 dr[i] = digit_of(k, shift, mask);
             }
@@ -886,7 +980,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                 const int s = wofs + 32 * i;
                 if (full || s < valid_in) {
                     U k = s_keys[s];
-                    if (desc.xin) k = map_fwd(k, map);
+                    if (desc.xin) k = rank_key(k, map, bias);
                     const uint32_t dig = dr[i] & 0xFFFFu;
                     const uint32_t pos = ((kVW == 2 && i >= H) ? wh1 : wh)[dig] + (dr[i] >> 16);
                     s_rkeys[pos] = k;
@@ -906,7 +1000,7 @@ __global__ void __launch_bounds__(BLOCK, onesweep_min_blocks(BLOCK, KPT)) radix_
                 const uint32_t dig = digit_of(k, shift, mask);
                 const size_t g = small_n ? (size_t)(uint32_t)(s_gbase32[dig] + (uint32_t)s)
                                          : (size_t)(s_gbase[dig] + (unsigned long long)s);
-                st_stream(dst + g, desc.xout ? map_inv(k, map) : k);
+                st_stream(dst + g, desc.xout ? unrank_key(k, map, bias) : k);
                 if (PAIRS) st_stream(vdst + g, s_rvals[s]);
             }
         }

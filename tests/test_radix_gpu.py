@@ -309,10 +309,14 @@ def test_adaptive_ranking(evo, dist, dtype):
 
 
 def test_adaptive_ranking_choice_per_pass(evo):
-    """Gaussian int64 keys (sd 1e6): the five top bytes take two values, so
-    passes 3..7 run match.any; passes 0..2 (spread digits, the first pass in
-    input order) run match masks."""
+    """Gaussian int64 keys (sd 1e6) with a few keys at both ends of the int64
+    range (so the span needs all eight digits and the sort is not rebased):
+    the five top bytes take two values for nearly every key, so passes 3..7
+    run match.any; passes 0..2 (spread digits, the first pass in input order)
+    run match masks."""
     x = gen("gaussian", ADAPT_N, torch.int64, seed=9)
+    x[::1_000_003] = torch.iinfo(torch.int64).min + 5
+    x[7::1_000_003] = torch.iinfo(torch.int64).max - 5
     y = torch.empty_like(x)
     evo.profile(True)
     try:
@@ -322,6 +326,7 @@ def test_adaptive_ranking_choice_per_pass(evo):
     finally:
         evo.profile(False)
     assert {r["pass"]: r["rank"] for r in recs} == {0: 3, 1: 3, 2: 3, 3: 1, 4: 1, 5: 1, 6: 1, 7: 1}
+    assert np.array_equal(bits(y), oracle.radix_sort(x.cpu().numpy()).view(np.uint64))
 
 
 def test_below_adaptive_size_single_launch_per_pass(evo):
