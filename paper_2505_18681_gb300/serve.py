@@ -306,21 +306,30 @@ def summarize(reqs, lam, label):
 
 def serve_mix(count: int, max_size: int = 100_000_000, streams: int = 4, load: float = 0.7, seed: int = 42,
               table: str | None = None, max_total: int | None = None) -> dict:
-    """The serving measurement: the mix served once with every request
-    arriving at once (capacity), then again with Poisson arrivals at `load`
-    times that capacity; p50/p99 latency and keys/s of the second run."""
+    """The serving measurement, on one server whose slots stay resident: the
+    mix served with every request arriving at once, first to warm up (slot
+    and pool growth, first launches) and then timed (capacity), then again
+    with Poisson arrivals at `load` times that capacity; p50/p99 latency and
+    keys/s of the Poisson run."""
     hi = size_upper_bound(count, 1000, max_size, max_total)
     reqs = make_requests(count, hi=max_size, seed=seed, max_total=max_total)
     srv = SortServer(streams=streams, use_table=table)
+
+    def reset():
+        for r in reqs:
+            r.admitted = r.launched = r.done = None
+        srv.done = []
+
+    srv.run(reqs, [0.0] * len(reqs))   # warm-up
+    reset()
     srv.run(reqs, [0.0] * len(reqs))
     cap = summarize(reqs, None, "saturated")
     lam = load * len(reqs) / cap["span_s"]
     g = torch.Generator().manual_seed(seed + 1)
     gaps = torch.empty(len(reqs), dtype=torch.float64).exponential_(lam, generator=g)
     arrivals = torch.cumsum(gaps, 0).tolist()
-    for r in reqs:
-        r.done = None
-    srv = SortServer(streams=streams, use_table=table)
+    reset()
+    srv.launches = 0
     srv.run(reqs, arrivals)
     res = summarize(reqs, lam, "poisson")
     res["capacity_requests_per_s"] = len(reqs) / cap["span_s"]
