@@ -409,7 +409,8 @@ typedef enum {
     EVOSORT_K_MERGE_PARTITION = 5,   /* merge-path split points */
     EVOSORT_K_MERGE_PASS = 6,        /* one pairwise merge round */
     EVOSORT_K_SEGMENTED = 7,         /* batched segmented sort kernels */
-    EVOSORT_K_SMALL = 8              /* one-CTA shared-memory sort of a small array */
+    EVOSORT_K_SMALL = 8,             /* one-CTA shared-memory sort of a small array */
+    EVOSORT_K_DICT = 9               /* few distinct keys: count (pass 0) and fill (pass 1) */
 } evosort_kernel_kind;
 
 typedef struct {

@@ -578,8 +578,18 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     if ((!p || p->algo == EVOSORT_ALGO_AUTO) && table_nonempty()) {
         void* st = p ? p->stream : nullptr;
         const bool desc = p && p->descending;
-        const evosort_status ps = plan_for(in, n, dt, st, desc, &planned, nullptr);
+        int cls = EVOSORT_CLASS_RANDOM;
+        std::vector<uint64_t> dict;
+        const evosort_status ps = plan_for(in, n, dt, st, desc, &planned, &cls, pairs ? nullptr : &dict);
         if (ps != EVOSORT_OK) return finish(ps, evosort_last_error());
+        // a few distinct keys in the sample (keys only): counting sort over
+        // those values, unless some key is not among them
+        if (!pairs && cls == EVOSORT_CLASS_FEW && !dict.empty() && n >= kDictMinKeys) {
+            bool done = false;
+            const int rcd = dict_sort(in, out, n, dt, desc, dict, (cudaStream_t)st, &done, &err);
+            if (rcd) return finish(rcd, err);
+            if (done) return EVOSORT_OK;
+        }
         if (p) {
             planned.stream = p->stream;
             planned.workspace = p->workspace;

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -43,12 +44,23 @@ uint32_t wait_limit();
 void set_error(const std::string& msg);
 void default_radix_plan(int dt, Plan* pl, size_t n = 0);
 bool table_nonempty();
-int classify_sample(const unsigned char* buf, size_t m, int dt, bool descending = false);
+// Largest distinct-value count of the dictionary path, and the smallest
+// array it is tried on (below that the radix sort's fixed cost is small).
+constexpr int kDictMax = 64;
+constexpr size_t kDictMinKeys = (size_t)1 << 16;
+// Class of a sample; with dict, the sample's distinct keys in the key map's
+// order (ascending) are stored there when there are at most kDictMax.
+int classify_sample(const unsigned char* buf, size_t m, int dt, bool descending = false,
+                    std::vector<uint64_t>* dict = nullptr);
 int classify_host(const void* keys, size_t n, int dt, bool descending = false);
 // evosort_plan for a sort in the given direction (the class is read in the
 // order the sort will produce)
 evosort_status plan_for(const void* keys, size_t n, int dt, void* stream, bool descending, evosort_params* out,
-                        int* cls_out);
+                        int* cls_out, std::vector<uint64_t>* dict = nullptr);
+// Counting sort over the sample's distinct keys (keys only): *done is false
+// when a key is not among them (the input is then untouched).
+int dict_sort(const void* in, void* out, size_t n, int dt, bool descending, const std::vector<uint64_t>& dict,
+              cudaStream_t s, bool* done, std::string* err);
 bool table_lookup(int dt, size_t n, int cls, evosort_params* out);
 
 void count_launches(uint64_t k);
