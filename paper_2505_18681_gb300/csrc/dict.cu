@@ -81,12 +81,25 @@ __global__ void __launch_bounds__(kDictThreads) dict_count(const U* keys, size_t
     const size_t tail0 = head + nvec * V;
     if (gtid < n - tail0) one(keys[tail0 + gtid]);
     const uint4* vp = (const uint4*)(keys + head);
-    for (size_t c = gtid; c < nvec; c += gthreads) {
-        const uint4 q = __ldcs(vp + c);
-        U k[V];
-        memcpy(k, &q, 16);
+    // grid-stride over 16-byte chunks, kUnroll chunks per step whose loads
+    // are all issued before the lookups (enough bytes in flight per SM)
+    constexpr int kUnroll = 4;
+    for (size_t c0 = gtid; c0 < nvec; c0 += gthreads * kUnroll) {
+        uint4 q[kUnroll];
 #pragma unroll
-        for (int j = 0; j < V; ++j) one(k[j]);
+        for (int u = 0; u < kUnroll; ++u) {
+            const size_t c = c0 + (size_t)u * gthreads;
+            if (c < nvec) q[u] = __ldcs(vp + c);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (c0 + (size_t)u * gthreads < nvec) {
+                U k[V];
+                memcpy(k, &q[u], 16);
+#pragma unroll
+                for (int j = 0; j < V; ++j) one(k[j]);
+            }
+        }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(miss, 1u);
     __syncthreads();
