@@ -350,7 +350,7 @@ evosort_status evosort_tune(const void* sample, size_t n, evosort_dtype dt, cons
  * on each device the first time this entry point runs there (or when the
  * library's module is loaded, if the CUDA runtime's lazy loading is off) and
  * held until the process exits.  Sizes whose scratch exceeds it (above about
- * 7.7 million 64-bit or 15.8 million 32-bit keys) are rejected with
+ * 7.7 million 64-bit or 14.9 million 32-bit keys) are rejected with
  * EVOSORT_ERR_INVALID before anything is launched.
  * The first call on each device looks up the buffer's device address (once,
  * with that device current); make that first call before any stream capture.
