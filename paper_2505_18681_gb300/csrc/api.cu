@@ -579,15 +579,23 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
         void* st = p ? p->stream : nullptr;
         const bool desc = p && p->descending;
         int cls = EVOSORT_CLASS_RANDOM;
-        std::vector<uint64_t> dict;
-        const evosort_status ps = plan_for(in, n, dt, st, desc, &planned, &cls, pairs ? nullptr : &dict);
+        SampleInfo info;
+        const evosort_status ps = plan_for(in, n, dt, st, desc, &planned, &cls, &info);
         if (ps != EVOSORT_OK) return finish(ps, evosort_last_error());
         // a few distinct keys in the sample (keys only): counting sort over
         // those values, unless some key is not among them
-        if (!pairs && cls == EVOSORT_CLASS_FEW && !dict.empty() && n >= kDictMinKeys) {
+        if (!pairs && cls == EVOSORT_CLASS_FEW && !info.dict.empty() && n >= kDictMinKeys) {
             bool done = false;
-            const int rcd = dict_sort(in, out, n, dt, desc, dict, (cudaStream_t)st, &done, &err);
+            const int rcd = dict_sort(in, out, n, dt, desc, info.dict, (cudaStream_t)st, &done, &err);
             if (rcd) return finish(rcd, err);
+            if (done) return EVOSORT_OK;
+        }
+        // a sample in order (or in reverse order): copy checked on the way,
+        // unless some key is out of order
+        if (info.order != 0 && n >= kDictMinKeys) {
+            bool done = false;
+            const int rco = ordered_sort(in, out, vin, vout, n, dt, desc, info.order, (cudaStream_t)st, &done, &err);
+            if (rco) return finish(rco, err);
             if (done) return EVOSORT_OK;
         }
         if (p) {
@@ -601,6 +609,21 @@ static evosort_status sort_common(const void* in, void* out, const uint32_t* vin
     Plan pl;
     int rc = resolve(p, dt, pairs, &pl, &err, n);
     if (rc) return finish(rc, err);
+    auto tile_fits = [&](const Plan& q) {
+        if (q.algo != EVOSORT_ALGO_RADIX) return true;
+        if (q.pass_kernel == 2)
+            return reg_config_fits(w, pairs, q.block_size, q.keys_per_thread, q.digit_bits, q.rank_mode);
+        return onesweep_config_fits(w, pairs, q.block_size, q.keys_per_thread, q.digit_bits, q.rank_mode) &&
+               onesweep_rank_fits(q.rank_mode, q.block_size, q.keys_per_thread, w, pairs, q.digit_bits);
+    };
+    if (p == &planned && !tile_fits(pl)) {
+        // the tables are tuned on keys alone: a tile that cannot also hold the
+        // values gives way to the default tile rule for this sort
+        planned.block_size = planned.keys_per_thread = 0;
+        planned.pass_kernel = 0;
+        rc = resolve(p, dt, pairs, &pl, &err, n);
+        if (rc) return finish(rc, err);
+    }
     if (pl.algo == EVOSORT_ALGO_RADIX && pl.pass_kernel == 2 &&
         !reg_config_fits(w, pairs, pl.block_size, pl.keys_per_thread, pl.digit_bits, pl.rank_mode))
         return finish(EVOSORT_ERR_INVALID, "register-tile radix pass (pass_kernel 2): needs 8-bit digits, rank mode "

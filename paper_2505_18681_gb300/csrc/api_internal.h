@@ -45,22 +45,34 @@ void set_error(const std::string& msg);
 void default_radix_plan(int dt, Plan* pl, size_t n = 0);
 bool table_nonempty();
 // Largest distinct-value count of the dictionary path, and the smallest
-// array it is tried on (below that the radix sort's fixed cost is small).
+// array it and the ordered path are tried on (below that the radix sort's
+// fixed cost is small).
 constexpr int kDictMax = 64;
 constexpr size_t kDictMinKeys = (size_t)1 << 16;
-// Class of a sample; with dict, the sample's distinct keys in the key map's
-// order (ascending) are stored there when there are at most kDictMax.
+// What a sample shows beyond its class: its distinct keys in the key map's
+// order (ascending) when there are at most kDictMax, and whether every
+// neighbour pair is non-decreasing (order 1), non-increasing (-1) or neither.
+struct SampleInfo {
+    std::vector<uint64_t> dict;
+    int order = 0;
+};
 int classify_sample(const unsigned char* buf, size_t m, int dt, bool descending = false,
-                    std::vector<uint64_t>* dict = nullptr);
+                    SampleInfo* info = nullptr);
 int classify_host(const void* keys, size_t n, int dt, bool descending = false);
 // evosort_plan for a sort in the given direction (the class is read in the
 // order the sort will produce)
 evosort_status plan_for(const void* keys, size_t n, int dt, void* stream, bool descending, evosort_params* out,
-                        int* cls_out, std::vector<uint64_t>* dict = nullptr);
+                        int* cls_out, SampleInfo* info = nullptr);
 // Counting sort over the sample's distinct keys (keys only): *done is false
 // when a key is not among them (the input is then untouched).
 int dict_sort(const void* in, void* out, size_t n, int dt, bool descending, const std::vector<uint64_t>& dict,
               cudaStream_t s, bool* done, std::string* err);
+// Copy (or reversed copy, keys only) of an input the sample shows in order
+// (hint 1) or in reverse order (hint -1), checked on the way: *done is false
+// when some key is out of order (the output is then to be rewritten; the
+// input is untouched).
+int ordered_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt, bool descending,
+                 int hint, cudaStream_t s, bool* done, std::string* err);
 bool table_lookup(int dt, size_t n, int cls, evosort_params* out);
 
 void count_launches(uint64_t k);

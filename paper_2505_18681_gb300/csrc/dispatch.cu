@@ -48,9 +48,10 @@ uint64_t host_map(uint64_t u, int dt, bool descending) {
 
 // Class of a sample of m keys (raw bytes, m x key width), taken at stride
 // n / m from an array of n keys, read in the order of the sort's direction.
-// With dict, the distinct sampled keys (mapped, ascending) are stored there
-// when there are at most kDictMax of them (else it is left empty).
-int classify_sample(const unsigned char* buf, size_t m, int dt, bool descending, std::vector<uint64_t>* dict) {
+// With info, the distinct sampled keys (mapped, ascending) when there are at
+// most kDictMax of them, and the sample's order (1: no pair falls, -1: no
+// pair rises, 0: both happen).
+int classify_sample(const unsigned char* buf, size_t m, int dt, bool descending, SampleInfo* info) {
     const int w = dtype_bytes(dt);
     std::vector<uint64_t> raw(m, 0);
     for (size_t i = 0; i < m; ++i) {
@@ -71,9 +72,10 @@ int classify_sample(const unsigned char* buf, size_t m, int dt, bool descending,
     std::vector<uint64_t> sorted(raw);
     std::sort(sorted.begin(), sorted.end());
     const size_t distinct = std::unique(sorted.begin(), sorted.end()) - sorted.begin();
-    if (dict) {
-        dict->clear();
-        if (distinct <= (size_t)kDictMax) dict->assign(sorted.begin(), sorted.begin() + distinct);
+    if (info) {
+        info->dict.clear();
+        if (distinct <= (size_t)kDictMax) info->dict.assign(sorted.begin(), sorted.begin() + distinct);
+        info->order = down == 0 ? 1 : (up == 0 ? -1 : 0);
     }
     // top-byte concentration: share of the sample in the most common top byte
     size_t top[256] = {0};
@@ -133,7 +135,7 @@ bool table_nonempty() {
 // Class of keys[0..n) (a device array) from a strided sample, read in the
 // order of the sort's direction (synchronises the stream).
 evosort_status classify_device(const void* keys, size_t n, int dt, void* stream, bool descending,
-                                        int* cls, std::vector<uint64_t>* dict = nullptr) {
+                                        int* cls, SampleInfo* info = nullptr) {
     set_error("");
     if (!cls || (n && !keys) || dt < EVOSORT_I32 || dt > EVOSORT_F64) {
         set_error("evosort_classify: bad argument");
@@ -155,12 +157,12 @@ evosort_status classify_device(const void* keys, size_t n, int dt, void* stream,
         set_error(std::string("evosort_classify: sample copy: ") + cudaGetErrorString(e));
         return EVOSORT_ERR_CUDA;
     }
-    *cls = classify_sample(buf.data(), m, dt, descending, dict);
+    *cls = classify_sample(buf.data(), m, dt, descending, info);
     return EVOSORT_OK;
 }
 
 evosort_status plan_for(const void* keys, size_t n, int dt, void* stream, bool descending,
-                                 evosort_params* out, int* cls_out, std::vector<uint64_t>* dict) {
+                                 evosort_params* out, int* cls_out, SampleInfo* info) {
     set_error("");
     if (!out) {
         set_error("evosort_plan: null output");
@@ -170,7 +172,7 @@ evosort_status plan_for(const void* keys, size_t n, int dt, void* stream, bool d
     out->stream = stream;
     int cls = EVOSORT_CLASS_RANDOM;
     if (table_nonempty() && n >= 2) {
-        const evosort_status st = classify_device(keys, n, dt, stream, descending, &cls, dict);
+        const evosort_status st = classify_device(keys, n, dt, stream, descending, &cls, info);
         if (st != EVOSORT_OK) return st;
         if (table_lookup(dt, n, cls, out)) out->stream = stream;
         out->descending = descending ? 1 : 0;
