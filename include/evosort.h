@@ -225,6 +225,31 @@ evosort_status evosort_segmented_sort(void* keys, size_t total, const uint64_t* 
 /* Scratch bytes evosort_segmented_sort needs for total keys in nseg segments. */
 size_t evosort_segmented_workspace_bytes(size_t total, size_t nseg, evosort_dtype dt);
 
+/* ---- Per-rank steps of a multi-GPU sort of one array ---------------------
+ * Not in the paper (it names an MPI extension as future work).  Each rank
+ * holds a slice of the keys; the ranks agree on the part of the key range
+ * each owns from the slices' key ranges and range histograms (reduced over
+ * the ranks by the caller), exchange keys, and sort what they receive.
+ * Keys are compared in the order-preserving key space of dt (descending:
+ * that order reversed); "mapped" values below are keys in that space,
+ * zero-extended to 64 bits.  Asynchronous on stream (NULL: legacy default).
+ *
+ * evosort_key_range: range[0] = the smallest, range[1] = the largest mapped
+ * key of keys[0..n) (DEVICE array of 2 words, overwritten; n = 0 leaves
+ * range[0] = 2^64 - 1 and range[1] = 0). */
+evosort_status evosort_key_range(const void* keys, size_t n, evosort_dtype dt, int descending,
+                                 unsigned long long* range, void* stream);
+
+/* evosort_range_histogram: adds to counts[b] (DEVICE array of nbins words,
+ * not cleared) the number of keys with (mapped key - base) >> shift == b,
+ * a value at or above nbins counting in bin nbins - 1.  nbins 1..8192,
+ * 0 <= shift < key bits.  With base the smallest key over all ranks and
+ * shift making (largest - base) >> shift < nbins, the bins split the whole
+ * range into nbins ordered parts. */
+evosort_status evosort_range_histogram(const void* keys, size_t n, evosort_dtype dt, int descending,
+                                       unsigned long long base, int shift, int nbins, unsigned long long* counts,
+                                       void* stream);
+
 /* ---- Dispatcher and tuned table (Algorithm 5, AdaptivePartitionSort) ----
  * With params == NULL or params->algo == EVOSORT_ALGO_AUTO and a non-empty
  * table, a sort call classifies its input from a strided sample of 4096 keys

@@ -119,6 +119,10 @@ def library():
             lib.evosort_segmented_sort.restype = st
             lib.evosort_segmented_workspace_bytes.argtypes = [sz, sz, i]
             lib.evosort_segmented_workspace_bytes.restype = sz
+            lib.evosort_key_range.argtypes = [vp, sz, i, i, vp, vp]
+            lib.evosort_key_range.restype = st
+            lib.evosort_range_histogram.argtypes = [vp, sz, i, i, ctypes.c_ulonglong, i, i, vp, vp]
+            lib.evosort_range_histogram.restype = st
             lib.evosort_classify.argtypes = [vp, sz, i, vp, ctypes.POINTER(ctypes.c_int)]
             lib.evosort_classify.restype = st
             lib.evosort_plan.argtypes = [vp, sz, i, vp, pp, ctypes.POINTER(ctypes.c_int)]
@@ -324,6 +328,29 @@ def set_wait_limit(polls: int) -> None:
 def segmented_workspace_bytes(total: int, nseg: int, dtype: torch.dtype) -> int:
     """Scratch bytes of a batched segmented sort of total keys in nseg segments."""
     return int(library().evosort_segmented_workspace_bytes(total, nseg, DTYPES[dtype]))
+
+
+def key_range(keys: torch.Tensor, descending: bool = False, stream=None) -> tuple:
+    """(smallest, largest) key of a device array in the library's
+    order-preserving key space, as Python ints (evosort_key_range)."""
+    _need_cuda(keys)
+    out = torch.empty(2, dtype=torch.int64, device=keys.device)
+    _check(library().evosort_key_range(keys.data_ptr(), keys.numel(), _dtype_code(keys), int(descending),
+                                       out.data_ptr(), _stream_handle(stream)))
+    lo, hi = out.cpu().tolist()
+    return lo & (2**64 - 1), hi & (2**64 - 1)
+
+
+def range_histogram(keys: torch.Tensor, base: int, shift: int, nbins: int, descending: bool = False,
+                    stream=None) -> torch.Tensor:
+    """Counts (int64 device tensor of nbins) of keys with (mapped key - base)
+    >> shift == b (evosort_range_histogram)."""
+    _need_cuda(keys)
+    counts = torch.zeros(nbins, dtype=torch.int64, device=keys.device)
+    _check(library().evosort_range_histogram(keys.data_ptr(), keys.numel(), _dtype_code(keys), int(descending),
+                                             ctypes.c_ulonglong(base & (2**64 - 1)), int(shift), int(nbins),
+                                             counts.data_ptr(), _stream_handle(stream)))
+    return counts
 
 
 def kernel_launches() -> int:

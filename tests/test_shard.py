@@ -17,6 +17,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+import oracle  # noqa: E402  (the repository root is on the path only from here on)
+
 
 def test_partition_covers_every_segment_once_and_balances():
     from paper_2505_18681_gb300 import inputs, shard
@@ -95,3 +97,108 @@ def test_two_gloo_ranks_sort_their_shares_into_the_oracle_result():
         res = dict(out)
     assert res["once"], "a segment was sorted by no rank or by two"
     assert res["equal"], "the assembled shards differ from the oracle's segmented sort"
+
+
+# ---------------------------------------------------------------------------
+# One array over several gloo ranks (sort_distributed), with the per-rank
+# steps done on the CPU by the oracle: the exchange logic (range and
+# histogram reductions, boundaries, run lengths, all-to-all) is what runs.
+# ---------------------------------------------------------------------------
+class _OracleOps:
+    """Per-rank steps on CPU tensors: keys mapped to the order-preserving
+    unsigned space of their integer type (sign bit flipped; descending:
+    complemented), sorted by the oracle."""
+
+    @staticmethod
+    def _mapped(keys, descending):
+        a = keys.numpy()
+        u = a.view(np.uint32 if a.dtype.itemsize == 4 else np.uint64)
+        if a.dtype.kind == "i":
+            u = u ^ (np.uint32(1 << 31) if a.dtype.itemsize == 4 else np.uint64(1 << 63))
+        return ~u if descending else u
+
+    def key_range(self, keys, descending):
+        if keys.numel() == 0:
+            return 2**64 - 1, 0
+        m = self._mapped(keys, descending)
+        return int(m.min()), int(m.max())
+
+    def histogram(self, keys, base, shift, nbins, descending):
+        m = self._mapped(keys, descending).astype(np.uint64)
+        b = ((m - np.uint64(base)) >> np.uint64(shift)).astype(np.int64)
+        return torch.from_numpy(np.bincount(np.minimum(b, nbins - 1), minlength=nbins).astype(np.int64))
+
+    def sort(self, keys, values, descending):
+        m = self._mapped(keys, descending)
+        idx = np.arange(keys.numel(), dtype=np.uint32)
+        _, perm = oracle.radix_sort(m, idx)
+        k = torch.from_numpy(keys.numpy()[perm.astype(np.int64)].copy())
+        v = None if values is None else torch.from_numpy(values.numpy()[perm.astype(np.int64)].copy())
+        return k, v
+
+
+def _dist_worker(rank, world, port, out, dtype_name, descending, pairs, n, dist_kind):
+    import torch.distributed as tdist
+    from paper_2505_18681_gb300 import shard
+    tdist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    dtype = getattr(torch, dtype_name)
+    g = torch.Generator().manual_seed(17)
+    if dist_kind == "near_zero":
+        full = torch.randint(-(1 << 20), 1 << 20, (n,), generator=g, dtype=torch.int64).to(dtype)
+    elif dist_kind == "few":
+        full = (torch.randint(0, 5, (n,), generator=g, dtype=torch.int64) * 1000 - 2000).to(dtype)
+    else:
+        info = torch.iinfo(dtype)
+        full = torch.randint(info.min, info.max, (n,), generator=g, dtype=torch.int64).to(dtype)
+    cuts = [n * r // world for r in range(world + 1)]
+    cuts[1] = max(cuts[1] - 7, 0)   # uneven slices
+    mine = full[cuts[rank]:cuts[rank + 1]].clone()
+    vals = torch.arange(cuts[rank], cuts[rank + 1], dtype=torch.int64).to(torch.int32).view(torch.uint32) \
+        if pairs else None
+    k, v = shard.sort_distributed(mine, vals, descending=descending, ops=_OracleOps(), nbins=256)
+    parts = [None] * world
+    tdist.all_gather_object(parts, (k.numpy(), None if v is None else v.view(torch.int32).numpy()))
+    if rank == 0:
+        keys = np.concatenate([p[0] for p in parts])
+        a = full.numpy()
+        u = a.view(np.uint32 if a.dtype.itemsize == 4 else np.uint64) ^ \
+            (np.uint32(1 << 31) if a.dtype.itemsize == 4 else np.uint64(1 << 63))
+        order_key = ~u if descending else u
+        _, perm = oracle.radix_sort(order_key, np.arange(n, dtype=np.uint32))
+        out["keys"] = bool(np.array_equal(keys, a[perm.astype(np.int64)]))
+        out["sizes"] = [len(p[0]) for p in parts]
+        if pairs:
+            vals_all = np.concatenate([p[1] for p in parts]).view(np.uint32)
+            out["values"] = bool(np.array_equal(vals_all, perm))
+    tdist.barrier()
+    tdist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,dtype_name,descending,pairs,dist_kind",
+                         [(2, "int64", False, False, "near_zero"), (3, "int32", False, True, "uniform"),
+                          (2, "int32", True, True, "few"), (3, "int64", True, False, "uniform")])
+def test_one_array_over_gloo_ranks(world, dtype_name, descending, pairs, dist_kind):
+    """The ranks' runs, concatenated in rank order, are the oracle's sort of
+    the whole array (stable for key / value sorts: values are the global
+    indices), and keys of both signs near zero still spread over the ranks."""
+    n = 30_011
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_dist_worker, args=(world, port, out, dtype_name, descending, pairs, n, dist_kind), nprocs=world,
+                 join=True)
+        res = dict(out)
+    assert res["keys"], "the ranks' runs differ from the oracle's sort of the whole array"
+    if pairs:
+        assert res["values"], "values are not the stable order of the keys"
+    if dist_kind != "few":
+        assert min(res["sizes"]) > n // world * 0.8, res["sizes"]
+
+
+def test_rank_boundaries_split_into_equal_shares():
+    from paper_2505_18681_gb300 import shard
+    h = torch.tensor([5, 0, 5, 10, 0, 0, 20])
+    assert shard.rank_boundaries(h, 2) == [0, 4, 7]
+    assert shard.rank_boundaries(h, 4) == [0, 3, 4, 7, 7]   # shares 10, 10, 20, 0: bins are not split
+    assert shard.rank_boundaries(torch.zeros(8, dtype=torch.int64), 3) == [0, 0, 0, 8]
+    assert shard.shift_for(0, 4096) == 0 and shard.shift_for(4095, 4096) == 0 and shard.shift_for(4096, 4096) == 1
