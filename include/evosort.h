@@ -154,13 +154,28 @@ size_t evosort_workspace_bytes(size_t n, evosort_dtype dt, int with_values,
  * algorithm, pass kernel, tile shape (with n known the default tile follows
  * the closed form fitted to the tuned tables over log10 n, guarded so that
  * small inputs still give half of the SMs a tile), ranking, thresholds.  The
- * dispatcher's table is not consulted (that needs the keys: evosort_plan).
- * Host only. */
+ * dispatcher's table is not consulted (that needs the keys: evosort_plan), and
+ * neither are the decisions taken from the data (the few-values and ordered
+ * paths, range reduction).  Host only. */
 evosort_status evosort_resolve(size_t n, evosort_dtype dt, int with_values, const evosort_params* p,
                                evosort_params* out);
 
 /* Sorts keys[0..n) in place (AdaptivePartitionSort, Algorithm 5).
- * keys: device array of n elements of dtype dt. */
+ * keys: device array of n elements of dtype dt.
+ * With p == NULL or p->algo AUTO: arrays of at most small_cap keys take the
+ * one-CTA path; otherwise, when a tuned table is loaded, the dispatcher reads
+ * a 4096-key strided sample back to the host (synchronising p->stream) and
+ * takes the table's entry for the sample's class, and two data-dependent
+ * paths come first (keys of at least 2^16 elements): a sample with at most
+ * 64 distinct keys is sorted by counting over those values (keys only), and
+ * a sample in order (or in reverse order, keys only) by one checked copy;
+ * each reads one small result back and falls back to the radix sort when a
+ * key proves the sample wrong.  Such AUTO calls cannot be captured into a
+ * CUDA graph; calls with explicit parameters (or no table) stay
+ * asynchronous.  In every radix sort the passes rank key - min when the
+ * keys' span needs fewer 8-bit digits than their raw digits that vary (a
+ * decision taken on the device).  Whatever the path, the result is the one
+ * sorted array. */
 evosort_status evosort_sort(void* keys, size_t n, evosort_dtype dt, const evosort_params* p);
 
 /* Out-of-place variant: reads keys_in, writes the sorted keys to keys_out.
