@@ -451,7 +451,8 @@ typedef enum {
     EVOSORT_K_SEGMENTED = 7,         /* batched segmented sort kernels */
     EVOSORT_K_SMALL = 8,             /* one-CTA shared-memory sort of a small array */
     EVOSORT_K_DICT = 9,              /* few distinct keys: count (pass 0) and fill (pass 1) */
-    EVOSORT_K_ORDERED = 10           /* input in order: checked copy (pass 0), check (1), reversed copy (2) */
+    EVOSORT_K_ORDERED = 10,          /* input in order: checked copy (pass 0), check (1), reversed copy (2) */
+    EVOSORT_K_RADIX_COUNT = 11       /* narrow key range: value count and fill (both launches in one record) */
 } evosort_kernel_kind;
 
 typedef struct {

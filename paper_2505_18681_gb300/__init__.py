@@ -83,7 +83,7 @@ class KernelRecord(ctypes.Structure):
 
 KERNEL_KINDS = {0: "radix_histogram", 1: "radix_scan", 2: "radix_onesweep", 3: "radix_fixup",
                 4: "merge_block", 5: "merge_partition", 6: "merge_pass", 7: "segmented", 8: "small", 9: "dict",
-                10: "ordered"}
+                10: "ordered", 11: "radix_count"}
 
 _lock = threading.Lock()
 _lib = None

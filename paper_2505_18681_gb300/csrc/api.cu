@@ -165,7 +165,8 @@ struct RadixLayout {
     int npass;
     size_t ntiles;
     int lb64;
-    size_t off_desc, off_tiles, off_counts, off_range, off_counts2, off_lookback, zero_end, off_tmp, off_vtmp, total;
+    size_t off_desc, off_tiles, off_counts, off_range, off_counts2, off_cbins, off_lookback, zero_end, off_tmp, off_vtmp,
+        total;
 };
 
 static RadixLayout radix_layout(size_t n, int w, bool pairs, const Plan& pl) {
@@ -186,6 +187,8 @@ static RadixLayout radix_layout(size_t n, int w, bool pairs, const Plan& pl) {
     off = align_up(off + RNG_WORDS * sizeof(unsigned long long), 256);
     L.off_counts2 = off;   // digit counts of the rebased keys (8-bit digits only)
     off = align_up(off + (pl.digit_bits == 8 ? L.npass * bins * sizeof(unsigned long long) : 0), 256);
+    L.off_cbins = off;   // value bins of the narrow-range counting sort (keys only, 8-bit digits)
+    off = align_up(off + (pl.digit_bits == 8 && !pairs ? counting_bins_bytes() : 0), 256);
     L.off_lookback = off;
     off = align_up(off + (size_t)L.npass * L.ntiles * bins * (L.lb64 ? 8 : 4), 256);
     L.zero_end = off;
@@ -269,6 +272,13 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
         ProfScope ps(call, EVOSORT_K_RADIX_SCAN, -1, 0.0, 0, s);
         if (e == cudaSuccess) e = launch_radix_aux(w, 1, 1, 0, s, a, inplace);
     }
+    if (pl.digit_bits == 8 && !pairs) {
+        // narrow key range: counting sort in place of the passes (decided on
+        // the device; the two kernels return at once otherwise)
+        ProfScope ps(call, EVOSORT_K_RADIX_COUNT, -1, 0.0, n, s);
+        if (e == cudaSuccess)
+            e = launch_radix_counting(w, a, (unsigned long long*)(base + L.off_cbins), s);
+    }
     const bool reg = pl.pass_kernel == 2;
     for (int p = 0; p < L.npass && e == cudaSuccess; ++p) {
         for (int v = 0; v < (adapt ? 2 : 1) && e == cudaSuccess; ++v) {
@@ -291,7 +301,8 @@ int radix_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, s
         if (e == cudaSuccess) e = launch_radix_aux(w, 2, fix_grid, 0, s, a, inplace);
     }
     prof_call_end(call, s, a.desc);
-    count_launches(3 + (pl.digit_bits == 8 ? 1 : 0) + (adapt ? 2 : 1) * L.npass);
+    count_launches(3 + (pl.digit_bits == 8 ? 1 : 0) + (pl.digit_bits == 8 && !pairs ? 2 : 0) +
+                   (adapt ? 2 : 1) * L.npass);
     if (e != cudaSuccess) {
         *err = std::string("radix launch: ") + cudaGetErrorString(e);
         return EVOSORT_ERR_CUDA;

@@ -73,6 +73,13 @@ int dict_sort(const void* in, void* out, size_t n, int dt, bool descending, cons
 // input is untouched).
 int ordered_sort(const void* in, void* out, const uint32_t* vin, uint32_t* vout, size_t n, int dt, bool descending,
                  int hint, cudaStream_t s, bool* done, std::string* err);
+// Counting sort of a narrow key range inside the radix path (keys only,
+// 8-bit digits): launched after K2, it decides on the device and, when it
+// applies, sorts and turns the passes off.  bins: counting_bins_bytes() of
+// zeroed scratch.
+struct RadixArgs;
+size_t counting_bins_bytes();
+cudaError_t launch_radix_counting(int w, const RadixArgs& a, unsigned long long* bins, cudaStream_t s);
 bool table_lookup(int dt, size_t n, int cls, evosort_params* out);
 
 void count_launches(uint64_t k);
