@@ -91,7 +91,7 @@ def _worker(rank, world, port, out):
 def test_two_gloo_ranks_sort_their_shares_into_the_oracle_result():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
@@ -183,7 +183,7 @@ def test_one_array_over_gloo_ranks(world, dtype_name, descending, pairs, dist_ki
     indices), and keys of both signs near zero still spread over the ranks."""
     n = 30_011
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_dist_worker, args=(world, port, out, dtype_name, descending, pairs, n, dist_kind), nprocs=world,
                  join=True)

@@ -108,7 +108,7 @@ def test_one_array_over_two_ranks_on_one_gpu(dtype_name, pairs):
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_gpu_dist_worker, args=(2, port, out, dtype_name, pairs), nprocs=2, join=True)
         res = dict(out)

@@ -102,7 +102,7 @@ def test_table_save_load_roundtrip(evo, tmp_path):
     assert evo.table_size() == 0
     evo.table_load(path)
     assert evo.table_size() == 3
-    text = open(path).read()
+    text = (tmp_path / "table.txt").read_text()
     assert "1 29 0 0 10" in text
     evo.table_clear()
     bad = tmp_path / "bad.txt"
