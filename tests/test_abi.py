@@ -132,3 +132,51 @@ def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         evo.library()
+
+
+def _largest_noalloc(lib, dt):
+    """Largest n whose default radix scratch fits 64 MiB (host arithmetic)."""
+    import paper_2505_18681_gb300 as evo
+    p = evo.make_params(algo="radix")
+    lo, hi = 1, 1 << 26
+    while lo < hi:
+        m = (lo + hi + 1) // 2
+        if lib.evosort_workspace_bytes(m, dt, 0, ctypes.byref(p)) <= 64 << 20:
+            lo = m
+        else:
+            hi = m - 1
+    return lo
+
+
+def test_noalloc_limit_matches_its_declaration(lib):
+    """The sizes the header quotes for the fixed 64 MiB buffer are the ones
+    the workspace arithmetic gives, and one key more is rejected on the host
+    (the pointers are never used: the size check comes first)."""
+    f = lib.evosort_sort_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    text = re.sub(r"\n\s*\*\s?", " ", open(os.path.join(ROOT, "include", "evosort.h")).read())
+    m = re.search(r"about\s+([\d.]+) million 64-bit or ([\d.]+) million 32-bit keys", text)
+    assert m, "the limit is quoted in the declaration"
+    for dt, quoted, w in ((1, float(m.group(1)), 8), (0, float(m.group(2)), 4)):
+        n = _largest_noalloc(lib, dt)
+        assert round(n / 1e6, 1) == quoted, (dt, n)
+        big = n + 1
+        assert f(FAKE, FAKE + big * w + 4096, big, dt, None) == 1
+        assert b"64 MiB" in lib.evosort_last_error()
+    assert f(FAKE, FAKE, 0, 1, None) == 0              # nothing to sort
+    assert f(FAKE, FAKE + 8, 10, 1, None) == 1         # overlapping
+    assert f(FAKE + 4, FAKE + 4096, 10, 1, None) == 1  # misaligned
+    assert f(FAKE, FAKE + 4096, 10, 9, None) == 1      # bad dtype
+
+
+def test_shard_entry_points_reject_bad_arguments(lib):
+    kr, rh = lib.evosort_key_range, lib.evosort_range_histogram
+    assert kr(None, 10, 1, 0, FAKE, None) == 1                       # null keys
+    assert kr(FAKE, 10, 9, 0, FAKE, None) == 1                       # bad dtype
+    assert kr(FAKE, 10, 1, 0, None, None) == 1                       # null range
+    for nbins, shift, dt in ((0, 0, 1), (8193, 0, 1), (16, 64, 1), (16, 32, 0), (16, -1, 1)):
+        assert rh(FAKE, 10, dt, 0, 0, shift, nbins, FAKE, None) == 1
+    assert rh(FAKE, 10, 1, 0, 0, 0, 16, None, None) == 1              # null counts
+    assert b"evosort_range_histogram: bad argument" in lib.evosort_last_error()
+    assert rh(None, 0, 1, 0, 0, 0, 16, FAKE, None) == 0               # nothing to count
