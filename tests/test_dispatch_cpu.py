@@ -161,3 +161,21 @@ def test_empty_table_or_single_key_is_not_sampled(evo):
     p, cls = evo.plan_host(torch.tensor([42], dtype=torch.int64))
     assert cls == "random" and p == defaults(evo)
     evo.table_clear()
+
+
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64], ids=str)
+def test_tuning_workloads_sample_as_their_class(evo, dtype):
+    """Each class's tuning workload is read as that class by the dispatcher,
+    so the entry the GA writes is the one the sample later selects.  For
+    32-bit keys the narrow class cannot occur (narrow16 takes every sample
+    with at most half the key bits varying); its workload reads as skewed."""
+    import importlib
+    from paper_2505_18681_gb300 import inputs
+    tm = importlib.import_module("paper_2505_18681_gb300.tune")
+    evo.table_clear()
+    evo.table_set(dtype, 20, "random", {"algo": 0})
+    for cls, dist in tm.REPRESENTATIVE.items():
+        x = inputs.generate(dist, N, dtype, seed=42, device="cpu")
+        want = "skewed" if (dtype == torch.int32 and cls == "narrow") else cls
+        assert evo.plan_host(x)[1] == want, (cls, dist)
+    evo.table_clear()
