@@ -27,6 +27,11 @@
  *    Errors found on the device (a bounded wait that ran out) are recorded in
  *    a device status word and returned by the next evosort_sync().
  *  - n == 0 returns EVOSORT_OK without touching the device.
+ *  - Devices: a call works on the device current in the calling thread.  The
+ *    kernels' shared-memory limits and occupancy are set up once per process,
+ *    on the first device a kernel runs on; a process that drives several GPUs
+ *    may get EVOSORT_ERR_CUDA from the launches of kernels with large shared
+ *    tiles on the others.  Use one process per GPU (as the multi-GPU sorts do).
  *
  * Total order of keys (the paper sorts signed integers and flips the sign bit
  * before the passes and back after, Algorithms 4a/4b):
