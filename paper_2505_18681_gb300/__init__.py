@@ -315,7 +315,7 @@ def workspace_bytes(n: int, dtype: torch.dtype, with_values: bool = False, **kw)
 
 def release() -> None:
     """Waits for the device and returns the library's pooled scratch memory
-    on the current device to the driver (evosort_release)."""
+    on the current device to the CUDA driver (evosort_release)."""
     _check(library().evosort_release())
 
 

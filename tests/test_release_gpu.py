@@ -1,5 +1,5 @@
 """evosort_release: the scratch a sort leaves reserved in the device's
-stream-ordered pool goes back to the driver, and sorts after the release
+stream-ordered pool goes back to the CUDA driver, and sorts after the release
 still match the CPU oracle.  (Memory management of this library; the paper
 has no counterpart.)"""
 import numpy as np
@@ -32,7 +32,7 @@ def test_release_returns_pooled_scratch(evo):
     evo.release()
     free1, _ = torch.cuda.mem_get_info()
     # the sort's scratch was back in the pool (freed in stream order at its
-    # end); trimming the pool hands at least that much to the driver
+    # end); trimming the pool hands at least that much to the CUDA driver
     assert free1 - free0 >= need // 2, (free0, free1, need)
     del x, y
     torch.cuda.empty_cache()
