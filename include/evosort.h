@@ -146,11 +146,16 @@ typedef struct {
                                  never */
 } evosort_params;
 
-/* Fills *p with the built-in defaults (radix, d = 8, no workspace, NULL stream). */
+/* Fills *p with the built-in defaults (radix, d = 8, no workspace, NULL stream).
+ * d = 8 is the paper's fixed digit (one byte per pass, Algorithms 4a/4b); the
+ * other defaults are the GA's winners on this GPU (Algorithm 2). */
 void evosort_default_params(evosort_params* p);
 
 /* Bytes of scratch one call needs for n keys of dtype dt (with_values != 0 for
- * key/value sorts) under params p (NULL = defaults). */
+ * key/value sorts) under params p (NULL = defaults): the temporary array the
+ * passes of Algorithms 4a/4b (or the merge rounds of Algorithm 3) write into,
+ * plus the digit counts and look-back slots.  The paper allocates these inside
+ * the sort; here a caller may supply them.  Host only; 0 for bad params. */
 size_t evosort_workspace_bytes(size_t n, evosort_dtype dt, int with_values,
                                const evosort_params* p);
 
@@ -161,7 +166,8 @@ size_t evosort_workspace_bytes(size_t n, evosort_dtype dt, int with_values,
  * small inputs still give half of the SMs a tile), ranking, thresholds.  The
  * dispatcher's table is not consulted (that needs the keys: evosort_plan), and
  * neither are the decisions taken from the data (the few-values and ordered
- * paths, range reduction).  Host only. */
+ * paths, range reduction).  Host only.  The paper has no counterpart: its
+ * parameters are the GA genome of Section 4.2, fixed per run. */
 evosort_status evosort_resolve(size_t n, evosort_dtype dt, int with_values, const evosort_params* p,
                                evosort_params* out);
 
@@ -183,19 +189,24 @@ evosort_status evosort_resolve(size_t n, evosort_dtype dt, int with_values, cons
  * sorted array. */
 evosort_status evosort_sort(void* keys, size_t n, evosort_dtype dt, const evosort_params* p);
 
-/* Out-of-place variant: reads keys_in, writes the sorted keys to keys_out.
- * keys_in is left unchanged.  keys_in == keys_out is the in-place sort; any
+/* Out-of-place variant of evosort_sort (Algorithm 5 with the same paths):
+ * reads keys_in, writes the sorted keys to keys_out.  keys_in is left unchanged.  keys_in == keys_out is the in-place sort; any
  * other overlap is an error. */
 evosort_status evosort_sort_to(const void* keys_in, void* keys_out, size_t n, evosort_dtype dt,
                                const evosort_params* p);
 
 /* Stable key/value sort in place: values[i] travels with keys[i]; among equal
  * keys the input order of the values is kept (argsort when values are
- * 0..n-1).  values: device array of n uint32. */
+ * 0..n-1).  values: device array of n uint32.  The paper sorts keys alone; the
+ * stable placement of Algorithms 4a/4b (and the left-first merge of
+ * Algorithm 3) carries the value with its key. */
 evosort_status evosort_sort_pairs(void* keys, uint32_t* values, size_t n, evosort_dtype dt,
                                   const evosort_params* p);
 
-/* Out-of-place key/value sort. */
+/* Out-of-place key/value sort (as evosort_sort_pairs); the inputs are left
+ * unchanged.  keys_in == keys_out with values_in == values_out is the in-place
+ * sort; keys and values must be both in place or both out of place, and an
+ * input that partly overlaps its own output is an error. */
 evosort_status evosort_sort_pairs_to(const void* keys_in, const uint32_t* values_in, void* keys_out,
                                      uint32_t* values_out, size_t n, evosort_dtype dt,
                                      const evosort_params* p);
@@ -242,7 +253,8 @@ evosort_status evosort_sort_host_batch(const void* const* keys_in, void* const* 
 evosort_status evosort_segmented_sort(void* keys, size_t total, const uint64_t* offsets, size_t nseg,
                                       evosort_dtype dt, const evosort_params* p);
 
-/* Scratch bytes evosort_segmented_sort needs for total keys in nseg segments. */
+/* Scratch bytes evosort_segmented_sort needs for total keys in nseg segments
+ * (its work list and one key buffer of total keys; not in the paper). */
 size_t evosort_segmented_workspace_bytes(size_t total, size_t nseg, evosort_dtype dt);
 
 /* ---- Per-rank steps of a multi-GPU sort of one array ---------------------
@@ -444,7 +456,8 @@ const char* evosort_last_error(void);
  * traffic (keys and values read plus written); it is 0 for a radix pass whose
  * digit was constant (skipped on the device) and for a copy that was not
  * needed.  Events add a few microseconds per launch; leave this off outside
- * measurements. */
+ * measurements.  Not in the paper (it times whole sorts, Section 5): this is
+ * how the roofline of each kernel is measured. */
 typedef enum {
     EVOSORT_K_RADIX_HISTOGRAM = 0,   /* all-digit histogram (one key read) */
     EVOSORT_K_RADIX_SCAN = 1,        /* digit-count prefix sums + pass plan */
