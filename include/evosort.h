@@ -203,8 +203,9 @@ evosort_status evosort_sort_to(const void* keys_in, void* keys_out, size_t n, ev
 evosort_status evosort_sort_pairs(void* keys, uint32_t* values, size_t n, evosort_dtype dt,
                                   const evosort_params* p);
 
-/* Out-of-place key/value sort (as evosort_sort_pairs); the inputs are left
- * unchanged.  keys_in == keys_out with values_in == values_out is the in-place
+/* Out-of-place key/value sort (as evosort_sort_pairs: the stable placement of
+ * Algorithms 4a/4b, or Algorithm 3, carrying each value with its key); the
+ * inputs are left unchanged.  keys_in == keys_out with values_in == values_out is the in-place
  * sort; keys and values must be both in place or both out of place, and an
  * input that partly overlaps its own output is an error. */
 evosort_status evosort_sort_pairs_to(const void* keys_in, const uint32_t* values_in, void* keys_out,

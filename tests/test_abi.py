@@ -180,3 +180,23 @@ def test_shard_entry_points_reject_bad_arguments(lib):
     assert rh(FAKE, 10, 1, 0, 0, 0, 16, None, None) == 1              # null counts
     assert b"evosort_range_histogram: bad argument" in lib.evosort_last_error()
     assert rh(None, 0, 1, 0, 0, 0, 16, FAKE, None) == 0               # nothing to count
+
+
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment (its own or its section's) names the part
+    of the paper it follows (an algorithm or section) or says the paper has
+    no counterpart."""
+    text = open(os.path.join(ROOT, "include", "evosort.h")).read()
+    cite = re.compile(r"Algorithm|Section|paper")
+    missing = []
+    decl = r"^(?:evosort_status|void|size_t|int|uint64_t|const char\*)\s+(evosort_\w+)\s*\("
+    for m in re.finditer(decl, text, re.M):
+        before = text[:m.start()]
+        end = before.rfind("*/")
+        own = before[before.rfind("/*", 0, end):end] if end != -1 else ""
+        sec_at = before.rfind("/* ----")
+        section = text[sec_at:text.find("*/", sec_at)] if sec_at != -1 else ""
+        if not (cite.search(own) or cite.search(section)):
+            missing.append(m.group(1))
+    assert not missing, missing
+    assert len(declared_symbols()) >= 30
