@@ -715,7 +715,9 @@ evosort_status evosort_resolve(size_t n, evosort_dtype dt, int with_values, cons
     out->adapt_later = pl.adapt_later;
     out->adapt_first = pl.adapt_first;
     out->seg_warp_cap = pl.seg_warp_cap;
-    out->small_cap = pl.small_cap;
+    // the one-CTA path is considered only when the choice is left to the
+    // dispatcher or a cut-over is given (sort_common); otherwise it is off
+    out->small_cap = (p && p->algo != EVOSORT_ALGO_AUTO && p->small_cap <= 1) ? 1 : pl.small_cap;
     out->seg_giant = pl.seg_giant;
     if (p) {
         out->stream = p->stream;

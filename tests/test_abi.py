@@ -200,3 +200,17 @@ def test_every_declaration_cites_its_passage():
             missing.append(m.group(1))
     assert not missing, missing
     assert len(declared_symbols()) >= 30
+
+
+def test_resolve_reports_when_the_small_path_applies():
+    """evosort_resolve reports small_cap as the sort applies it: the default
+    cut-over when the algorithm is left to the dispatcher, off (1) for an
+    explicit algorithm unless a cut-over is given."""
+    import torch
+    import paper_2505_18681_gb300 as evo
+    assert evo.resolve(1000, torch.int32)["small_cap"] == 4096
+    assert evo.resolve(1000, torch.int32, algo="auto")["small_cap"] == 4096
+    assert evo.resolve(1000, torch.int32, algo="radix")["small_cap"] == 1
+    assert evo.resolve(1000, torch.int64, algo="merge")["small_cap"] == 1
+    assert evo.resolve(1000, torch.int32, algo="radix", small_cap=2048)["small_cap"] == 2048
+    assert evo.resolve(1000, torch.int32, algo="auto", small_cap=1)["small_cap"] == 1
