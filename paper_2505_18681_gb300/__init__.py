@@ -179,6 +179,9 @@ def _dtype_code(t: torch.Tensor) -> int:
 
 
 def _need_cuda(*ts):
+    """Every tensor on the current CUDA device (the library launches there, so
+    another device's pointers would be read by the wrong GPU) and contiguous."""
+    dev = None
     for t in ts:
         if t is None:
             continue
@@ -186,6 +189,13 @@ def _need_cuda(*ts):
             raise ValueError("tensors must be on a CUDA device")
         if not t.is_contiguous():
             raise ValueError("tensors must be contiguous")
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError("tensors must be on one device (got %s and %s)" % (dev, t.device))
+    if dev is not None and dev.index != torch.cuda.current_device():
+        raise ValueError("tensors are on %s but the current device is cuda:%d (torch.cuda.set_device)"
+                         % (dev, torch.cuda.current_device()))
 
 
 def _stream_handle(stream) -> int:

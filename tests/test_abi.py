@@ -214,3 +214,32 @@ def test_resolve_reports_when_the_small_path_applies():
     assert evo.resolve(1000, torch.int64, algo="merge")["small_cap"] == 1
     assert evo.resolve(1000, torch.int32, algo="radix", small_cap=2048)["small_cap"] == 2048
     assert evo.resolve(1000, torch.int32, algo="auto", small_cap=1)["small_cap"] == 1
+
+
+class _FakeTensor:
+    """Stands in for a CUDA tensor in the binding's argument check."""
+
+    def __init__(self, index, contiguous=True, cuda=True):
+        import torch
+        self.device = torch.device("cuda", index)
+        self.is_cuda = cuda
+        self._contiguous = contiguous
+
+    def is_contiguous(self):
+        return self._contiguous
+
+
+def test_binding_wants_tensors_on_the_current_device(monkeypatch):
+    import torch
+    import paper_2505_18681_gb300 as evo
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 1)
+    evo._need_cuda(_FakeTensor(1), None, _FakeTensor(1))
+    with pytest.raises(ValueError, match="one device"):
+        evo._need_cuda(_FakeTensor(1), _FakeTensor(0))
+    with pytest.raises(ValueError, match="current device"):
+        evo._need_cuda(_FakeTensor(0))
+    with pytest.raises(ValueError, match="contiguous"):
+        evo._need_cuda(_FakeTensor(1, contiguous=False))
+    with pytest.raises(ValueError, match="CUDA device"):
+        evo._need_cuda(_FakeTensor(1, cuda=False))
+    evo._need_cuda(None)
