@@ -4,12 +4,16 @@
 // The genome holds the knobs that act on the sort this library runs:
 //   algo        radix or merge (the paper's A_code: 4 = radix, 3 = merge)
 //   digit_bits  radix digit width d in [4, 11] (the paper fixes 8)
-//   tile        radix CTA tile shape (threads x keys per thread)
-//   rank_mode   radix tile ranking variant
+//   kern        radix pass kernel: staged tile or register tile
+//   shape       radix CTA tile shape (threads x keys per thread)
+//   rank        radix tile ranking variant
 //   tins        mergesort insertion threshold T_insertion in [2, 2048],
 //               first generation drawn from [2, 256] (Section 4.2 bounds)
-// The paper's T_numpy (library sort below a size) has no counterpart: there
-// is no CPU fallback, and small inputs take the same GPU path.
+//   alater, afirst  the adaptive ranking's two thresholds
+//   small       the one-CTA small-array cut-over, the GPU form of the
+//               paper's T_numpy (a library sort below a size, Algorithm 5)
+//   sblock, swarp, sgiant  the segmented sort's tier cut-overs (tuned in the
+//               segmented mode only)
 // Fitness f(x) = device time of one sort of the sample with genome x (median
 // of `reps` CUDA-event timings); a genome whose output is wrong or whose
 // configuration is rejected gets +infinity.
