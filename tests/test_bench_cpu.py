@@ -135,3 +135,28 @@ def test_segmented_roofline_bytes_and_block_cap(tmp_path):
     (tmp_path / "none.txt").write_text("0 20 0 0 8 0 0 0 0 0 1.0\n")  # no segmented entry
     assert bench.segmented_block_cap(str(tmp_path / "none.txt"), 4, 1 << 20) == 8192
     assert bench.segmented_block_cap(str(tmp_path / "none.txt"), 8, 1 << 20) == 4096
+
+
+def test_reference_line_carries_the_contract_keys(monkeypatch, capsys):
+    """The reference arm's JSON line (the oracle on a bounded sample) has
+    every key of the benchmark line, with the metric and units of the GPU arm
+    and e2e moving no bytes between host and device."""
+    import json
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    args = type("A", (), {"dists": "uniform,gaussian", "cpu_sample": 2000, "warmup": 1, "steps": 2,
+                          "dtype": "int64", "gpus": 1})()
+    bench.reference_arm(args)
+    line = json.loads(capsys.readouterr().out.strip())
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "GKeys/s"
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    assert "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    e = line["e2e"]
+    assert e["value"] == line["value"] and e["unit"] == line["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
